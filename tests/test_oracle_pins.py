@@ -1,0 +1,208 @@
+"""Pins of the oracle against things other than itself (CPU only).
+
+Each test fixes part of the oracle to something the paper or the mathematics
+decides: the paper's two worked examples (integers printed in Sec. III), the
+character-projection count of a sector (group theory, independent of any
+representative search), the literal Eq. 2 vectors in configuration space,
+spectra of the unsymmetrised Hamiltonian, and closed forms (4-site ring, XX chain
+by free fermions).  The last group plants typical mistakes in a copy of the
+oracle's matrix elements and checks that a pin catches each of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import oracle
+import workloads as w
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")))
+
+
+def _bits(s):
+    return int("".join("1" if c == "u" else "0" for c in s), 2)
+
+
+# ---------------------------------------------------------------- worked examples
+def test_worked_example_two_sublattices():
+    g = GOLD["two_sublattices"]
+    p = w.chain(6, n_sublat=2, n_up=3)
+    s = _bits(g["state"])
+    assert s == g["state_int"]
+    assert (s >> 3) == g["substate_A"] and (s & 7) == g["substate_B"]
+    rep_a, _ = oracle.sublattice_tables(p, 2, 0, g["substate_A"])
+    rep_b, sym_b = oracle.sublattice_tables(p, 2, 1, g["substate_B"])
+    assert rep_a == g["Rep_A"] and rep_b == g["Rep_B"]
+    assert [f"T{k}" for k in sym_b] == g["Sym_B"]
+    # G_A / G_B: elements carrying sublattice A (resp. B) onto A
+    blk = lambda X: set(range(3 * X, 3 * X + 3))
+    GA = [f"T{k}" for k in range(6) if set(p.perm[k, :3].tolist()) == blk(0)]
+    GB = [f"T{k}" for k in range(6) if set(p.perm[k, 3:].tolist()) == blk(0)]
+    assert GA == g["G_A"] and GB == g["G_B"]
+    assert int(oracle.apply_sym(p, 1, [s])[0]) == g["representative_int"] == _bits(g["representative"])
+    rep, gmin, stab, kept = oracle.representatives(p, [s])
+    assert int(rep[0]) == g["representative_int"] and f"T{gmin[0]}" == g["g"]
+
+
+def test_worked_example_three_sublattices():
+    g = GOLD["three_sublattices"]
+    p = w.chain(6, n_sublat=3, n_up=3)
+    s = _bits(g["state"])
+    assert s == g["state_int"]
+    for X, name in enumerate("ABC"):
+        sub = (s >> (2 * (2 - X))) & 3
+        assert sub == g["substates"][name]
+        rep, sym = oracle.sublattice_tables(p, 3, X, sub)
+        assert rep == g["Rep"][name]
+        assert [f"T{k}" for k in sym] == g["Sym"][name]
+    for name, val in g["candidates"].items():
+        assert int(oracle.apply_sym(p, int(name[1:]), [s])[0]) == val
+    rep, gmin, _, _ = oracle.representatives(p, [s])
+    assert int(rep[0]) == g["representative_int"] == _bits(g["representative"])
+    assert f"T{gmin[0]}" == g["g"]
+
+
+def test_representative_is_orbit_minimum_bruteforce():
+    # the orbit computed by a separate route: repeated application of the generator T1
+    p = w.chain(10, n_up=4)
+    states = oracle.core._sector_states(10, 4)
+    rep, g, stab, kept = oracle.representatives(p, states)
+    for s, r, t in zip(states.tolist(), rep.tolist(), stab.tolist()):
+        orbit, x = [], s
+        for _ in range(10):
+            orbit.append(x)
+            x = ((x >> 1) | ((x & 1) << 9))          # move every spin one site along
+        assert r == min(orbit)
+        assert t == sum(1 for o in orbit if o == r)
+
+
+# ---------------------------------------------------------------- dimensions
+@pytest.mark.parametrize("mk", [
+    lambda: [w.chain(16, n_sublat=2, k=k, n_up=8) for k in range(16)],
+    lambda: [w.chain(12, n_sublat=3, k=k, n_up=5) for k in range(12)],
+    lambda: [w.square_torus(4, momentum=m, point_irrep=ir, n_sublat=4, J2=0.5, n_up=7)
+             for m in [(0, 0), (1, 0), (1, 1), (2, 2), (0, 2)]
+             for ir in range(w.n_point_irreps((4, 0), (0, 4), m))],
+])
+def test_dimension_matches_projection_count(mk):
+    for p in mk():
+        b, stab = oracle.basis(p)
+        assert b.size == oracle.dimension_formula(p), p.name
+        assert np.all(np.diff(b.astype(np.float64)) > 0)
+
+
+def test_abelian_sector_dims_add_up():
+    tot = sum(oracle.basis(w.chain(16, 2, k=k, n_up=8))[0].size for k in range(16))
+    assert tot == math.comb(16, 8)
+
+
+# ---------------------------------------------------------------- Eq. 2 literally
+@pytest.mark.parametrize("p", [
+    w.chain(10, 2, k=0, n_up=5), w.chain(10, 2, k=3, n_up=5), w.chain(10, 1, k=5, n_up=4),
+    w.chain(12, 2, k=4, n_up=6, Jz=0.3),
+    w.square_torus(3, momentum=(0, 0), point_irrep=1, n_sublat=1, J2=0.4, n_up=4),
+    w.square_torus(3, momentum=(1, 0), point_irrep=1, n_sublat=1, J2=0.4, n_up=4),
+    w.square_torus(3, momentum=(1, 2), point_irrep=0, n_sublat=1, J2=0.4, n_up=5),
+])
+def test_matrix_elements_equal_literal_projection(p):
+    H, bs, stab = oracle.hamiltonian(p)
+    Hp, bs2, dropped = oracle.projected_hamiltonian(p)
+    assert np.array_equal(bs, bs2)
+    assert dropped < 1e-12                    # dropped representatives have vanishing norm
+    assert np.abs(H.toarray() - Hp).max() < 1e-13
+
+
+# ---------------------------------------------------------------- spectra
+def test_union_of_momentum_spectra_is_full_spectrum():
+    N = 12
+    Hf, _ = w and oracle.full_hamiltonian(w.chain(N, 1, n_up=6))
+    full = np.linalg.eigvalsh(Hf.toarray())
+    ev = []
+    for k in range(N):
+        H, _, _ = oracle.hamiltonian(w.chain(N, 2, k=k, n_up=6))
+        Hd = H.toarray()
+        assert np.abs(Hd - Hd.conj().T).max() < 1e-14
+        ev.extend(np.linalg.eigvalsh(Hd))
+    assert len(ev) == len(full)
+    assert np.abs(np.sort(ev) - full).max() < 1e-11
+
+
+def test_c4v_sector_spectra_inside_full_spectrum():
+    base = dict(n_sublat=1, J2=0.45, n_up=4)
+    Hf, _ = oracle.full_hamiltonian(w.square_torus(3, **base))
+    full = np.linalg.eigvalsh(Hf.toarray())
+    for m in w.momenta((3, 0), (0, 3)):
+        for ir in range(w.n_point_irreps((3, 0), (0, 3), m)):
+            H, _, _ = oracle.hamiltonian(w.square_torus(3, momentum=m, point_irrep=ir, **base))
+            for e in np.linalg.eigvalsh(H.toarray()):
+                assert np.min(np.abs(full - e)) < 1e-11
+
+
+def test_four_site_ring_ground_state():
+    H, _, _ = oracle.hamiltonian(w.chain(4, 1, n_up=2))
+    assert abs(np.linalg.eigvalsh(H.toarray())[0] - (-2.0)) < 1e-14
+
+
+@pytest.mark.parametrize("N", [8, 12, 16])
+def test_xx_chain_free_fermion_ground_state(N):
+    # Jz = 0: Jordan-Wigner fermions at half filling, E0 = -J / sin(pi / N) for N % 4 == 0
+    e0 = min(np.linalg.eigvalsh(oracle.hamiltonian(w.chain(N, 2, k=k, n_up=N // 2, Jz=0.0))[0].toarray())[0]
+             for k in range(N))
+    assert abs(e0 + 1.0 / math.sin(math.pi / N)) < 1e-12
+
+
+def test_chain16_ground_state_against_unsymmetrised_lanczos():
+    Hf, _ = oracle.full_hamiltonian(w.chain(16, 1, n_up=8))
+    e_full = spla.eigsh(Hf, k=1, which="SA", tol=1e-14)[0][0]
+    e_sec = min(np.linalg.eigvalsh(oracle.hamiltonian(w.chain(16, 2, k=k, n_up=8))[0].toarray())[0]
+                for k in (0, 8))
+    assert abs(e_full - e_sec) < 1e-11
+
+
+def test_lanczos_matches_dense():
+    H, bs, _ = oracle.hamiltonian(w.config_chain16())
+    v0 = w.state_uniform(bs, 1805)
+    e, a, b, k = oracle.lanczos(lambda v: H @ v, v0)
+    assert abs(e - np.linalg.eigvalsh(H.toarray())[0]) < 1e-11
+
+
+def test_rows_equal_matrix_rows():
+    p = w.chain(12, 2, k=5, n_up=6)
+    H, bs, _ = oracle.hamiltonian(p)
+    x = w.state_uniform(bs, 7) + 1j * w.state_uniform(bs, 8)
+    xf = lambda s: w.state_uniform(s, 7) + 1j * w.state_uniform(s, 8)
+    y = oracle.rows(p, bs[::5], xf)
+    assert np.abs(y - (H @ x)[::5]).max() < 1e-13
+
+
+# ---------------------------------------------------------------- planted mistakes
+def _mutant_matrix(p, mutate):
+    bs, stab = oracle.basis(p)
+    diag, nt, reps, val = oracle.columns(p, bs)
+    D = bs.size
+    M = np.zeros((D, D), complex)
+    M[np.arange(D), np.arange(D)] = diag
+    for i in range(D):
+        for k in range(nt[i]):
+            j = int(np.searchsorted(bs, reps[i, k]))
+            M[j, i] += mutate(val[i, k], stab[i], stab[j])
+    return M
+
+
+@pytest.mark.parametrize("name,mutate", [
+    ("chi instead of chi*", lambda v, ti, tj: np.conj(v)),
+    ("no norm ratio", lambda v, ti, tj: v / math.sqrt(tj / ti)),
+    ("inverted norm ratio", lambda v, ti, tj: v * ti / tj),
+    ("sign of exchange", lambda v, ti, tj: -v),
+])
+def test_planted_mistakes_are_caught(name, mutate):
+    caught = False
+    for p in [w.chain(10, 2, k=3, n_up=5), w.chain(10, 2, k=0, n_up=5)]:
+        M = _mutant_matrix(p, mutate)
+        Hp, _, _ = oracle.projected_hamiltonian(p)
+        if np.abs(M - Hp).max() > 1e-8:
+            caught = True
+    assert caught, name
