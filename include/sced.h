@@ -1,0 +1,235 @@
+/*
+ * sced.h -- C ABI of libsced: the symmetry-adapted, matrix-free Hamiltonian-vector
+ * product of Wietek & Laeuchli, "Sublattice coding algorithm and distributed memory
+ * parallelization for large-scale exact diagonalizations of quantum many-body
+ * systems" (arXiv:1804.05028), on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Spin configurations are uint64 integers.  Site label 0 is the most significant
+ *    of the N used bits (bit N-1), an up spin is a 1, and states are ordered by
+ *    their integer value (Sec. II, Eq. 1 and the ordering by int).
+ *  - Sublattice X (0-based) is the block of labels [X*N/n_sublat, (X+1)*N/n_sublat);
+ *    sublattice 0 holds the most significant bits (Sec. III B, site numbering).
+ *  - Group element g carries the spin on label p to label perm[g*N + p]:
+ *    (g s)[perm[g*N+p]] = s[p].  One-dimensional irrep: chi(g) = exp(2 pi i
+ *    phase_num[g] / phase_denom) (Sec. II, Eq. 2, 1-D irreps only).
+ *  - Hamiltonian: H = sum_b J[c(b)] ( Jz[c(b)] S^z_i S^z_j + (S^+_i S^-_j + h.c.)/2 )
+ *    over bonds b = (i, j) of coupling class c(b) (Eq. 21 split into classes).
+ *  - Basis state |s_rho> = (1/N_s) sum_g chi(g)^* g|s> for each representative s
+ *    (Eq. 2) that survives the projection (chi = 1 on the stabiliser of s);
+ *    N_s = sqrt(|G| |Stab(s)|).  Its matrix elements are
+ *    <j|H_k|i> = c chi(h)^* N_j/N_i with s_j = h s' (Eq. 5; conjugation as implied
+ *    by Eq. 2).
+ *
+ * Errors: every call returns ED_OK (0) or one of the ED_ERR_* codes below and, on
+ * error, leaves a message for ed_last_error() (thread-local).  No call aborts the
+ * process.  Device work is enqueued on the caller's stream (a cudaStream_t passed
+ * as void*, NULL = the legacy default stream) on the device that is current when
+ * ed_build_basis ran; calls marked "synchronous" wait for it.
+ */
+#ifndef SCED_H
+#define SCED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ED_OK 0
+#define ED_ERR_INVALID 1     /* bad descriptor: N>64, non-bijective permutation, group not
+                                closed, bonds not invariant, chi not a homomorphism, ... */
+#define ED_ERR_UNSTABLE 2    /* sublattice split not stable under the group (Sec. III B,
+                                "Sublattice stability") or n_sublat does not divide N */
+#define ED_ERR_OOM 3         /* device or host allocation failed */
+#define ED_ERR_CUDA 4        /* a CUDA runtime call failed (message has the CUDA error) */
+#define ED_ERR_TIMEOUT 5     /* reserved: a bounded device wait gave up */
+#define ED_ERR_EMPTY 6       /* the sector has dimension 0 (Lanczos has nothing to do) */
+#define ED_ERR_UNSUPPORTED 7 /* valid request outside what this build implements */
+
+/* Vector element types of apply_H / lanczos. */
+#define ED_F64 0   /* double   */
+#define ED_F32 1   /* float    */
+#define ED_C128 2  /* complex double, interleaved (re, im) */
+#define ED_C64 3   /* complex float, interleaved (re, im) */
+
+/* Lattice: sites, sublattice split and bonds (Eq. 21).  Host memory, read only
+ * during ed_build_basis. */
+typedef struct {
+  int32_t n_sites;            /* N, 1..64 */
+  int32_t n_sublat;           /* number of sublattices, divides N; N/n_sublat <= 20 when > 1,
+                                 N <= 24 when 1 (one full lookup table, Sec. III) */
+  int32_t n_bonds;            /* 1..4096 */
+  int32_t n_classes;          /* coupling classes, 1..8 */
+  const int32_t *bonds;       /* [n_bonds][2] site labels, distinct */
+  const int32_t *bond_class;  /* [n_bonds] in [0, n_classes) */
+} ed_lattice;
+
+/* Symmetry group as site permutations (host memory). */
+typedef struct {
+  int32_t n_sym;              /* |G|, 1..65535 */
+  const int32_t *perm;        /* [n_sym][n_sites] */
+} ed_group;
+
+/* One-dimensional irrep as exact phases (host memory). */
+typedef struct {
+  int32_t phase_denom;        /* >= 1 */
+  const int32_t *phase_num;   /* [n_sym] */
+} ed_irrep;
+
+/* Tuning of the basis and its index; pass NULL for defaults. */
+typedef struct {
+  int32_t bucket_target;      /* average states per Limits bucket (default 4) */
+  int32_t reserved[7];
+} ed_basis_opts;
+
+typedef struct ed_basis ed_basis;   /* opaque; owns every device table it creates */
+
+typedef struct {
+  int64_t dim;                /* D, number of basis states */
+  int32_t is_real;            /* 1 when every character is +1 or -1 */
+  int32_t n_sites, n_sublat, n_sym, n_up, n_bonds, n_classes;
+  int32_t prefix_rank_bits;   /* top bits mapped through the prefix rank table */
+  int32_t prefix_raw_bits;    /* further bits of the Limits key */
+  int32_t postfix_bits;       /* bits compared by the in-bucket binary search */
+  int64_t n_keys;             /* Limits buckets */
+  int64_t max_bucket;         /* largest bucket */
+  int64_t table_bytes;        /* device bytes of Rep/Sym/SymmetryAction tables */
+  int64_t index_bytes;        /* device bytes of the prefix rank table, Limits and postfixes */
+  int64_t basis_bytes;        /* device bytes of Basis and |Stab| */
+  int64_t sym_list_len;       /* total entries of the Sym_X lists */
+  double build_ms;            /* wall time of ed_build_basis */
+} ed_basis_info_t;
+
+/*
+ * ed_build_basis -- validate the descriptor, build the sublattice-coding lookup
+ * tables (Alg. 1: Rep_X, Sym_X, SymmetryAction_X of Eqs. 8-11) on the host, then on
+ * the device enumerate every configuration with n_up up spins whose top block is its
+ * own Rep_0, keep those that are their own representative (Alg. 2) and survive the
+ * projection, in increasing integer order (Alg. 3 on one GPU: count, scan, fill), and
+ * build the index used by apply_H (Basis, |Stab| and the prefix map Limits of
+ * Sec. IV, with half-open buckets).
+ *   lattice, group, irrep: host descriptors (copied; caller keeps ownership).
+ *   n_up: number of up spins (S^z = n_up - N/2).
+ *   opts: NULL or tuning.  stream: enqueue on this stream; the call is synchronous.
+ *   out: receives the new basis (free with ed_free_basis), NULL on error.
+ * A sector of dimension 0 is valid: *out is a basis with dim 0.
+ * Errors: ED_ERR_INVALID, ED_ERR_UNSTABLE, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_UNSUPPORTED.
+ */
+int ed_build_basis(const ed_lattice *lattice, const ed_group *group, const ed_irrep *irrep,
+                   int32_t n_up, const ed_basis_opts *opts, void *stream, ed_basis **out);
+
+/* ed_free_basis -- release every device and host buffer of the basis (NULL is a no-op). */
+void ed_free_basis(ed_basis *basis);
+
+/* ed_basis_info -- sizes and index parameters of a basis (host struct, caller-owned). */
+int ed_basis_info(const ed_basis *basis, ed_basis_info_t *info);
+
+/* ed_basis_export -- synchronous copy of Basis (uint64[dim]) and |Stab| (uint16[dim]) to
+ * caller-owned HOST arrays; either pointer may be NULL. */
+int ed_basis_export(const ed_basis *basis, uint64_t *states, uint16_t *stab);
+
+/*
+ * ed_find_rep -- Alg. 2 (sublattice-coded representative search) plus the Limits
+ * lookup, for n arbitrary configurations.  All pointers are DEVICE arrays of length
+ * n owned by the caller: states (in), rep (out, Eq. 4 representative), sym (out, the
+ * first minimising group element in Sym_Y order; unique up to the stabiliser),
+ * stab (out, |Stab(rep)| = number of minimisers), index (out, position of rep in
+ * Basis, or -1 when rep is not a basis state: not a surviving representative or a
+ * different n_up).  Asynchronous on stream.  Output pointers may be NULL to skip.
+ */
+int ed_find_rep(const ed_basis *basis, const uint64_t *states, int64_t n, uint64_t *rep,
+                int32_t *sym, int32_t *stab, int64_t *index, void *stream);
+
+/*
+ * ed_apply_H -- y = H x on the symmetry-adapted basis, matrix-free (Sec. IV,
+ * Eqs. 12-17 restated as a row-wise pull): for each row i, its diagonal, then for
+ * each antiparallel bond the exchanged configuration, its representative by sublattice
+ * coding (Alg. 2), its index through Limits and a binary search in the bucket, and
+ * y_i += (J/2) chi(h) sqrt(|Stab_j|/|Stab_i|) x_j.  No atomics; every y_i is written
+ * once, with a fixed summation order (deterministic).
+ *   J, Jz: HOST arrays [n_classes].
+ *   x, y: DEVICE arrays of dim elements of `dtype` (ED_F64 or ED_F32; the complex types
+ *   for sectors with complex characters), caller-owned, must not overlap.
+ *   dtype ED_F32 stores vectors in float and accumulates each row in float.
+ *   Asynchronous on stream.  dim 0: no-op.
+ * Errors: ED_ERR_INVALID (null pointers, dtype not matching the sector), ED_ERR_CUDA.
+ */
+int ed_apply_H(const ed_basis *basis, const double *J, const double *Jz, const void *x,
+               void *y, int32_t dtype, void *stream);
+
+/*
+ * ed_apply_H_rows -- as ed_apply_H restricted to rows [row_begin, row_end): y holds
+ * those rows only (y[0] is row row_begin), x is the whole vector.  Building block of a
+ * row-sharded product across devices.
+ */
+int ed_apply_H_rows(const ed_basis *basis, const double *J, const double *Jz, const void *x,
+                    void *y, int32_t dtype, int64_t row_begin, int64_t row_end, void *stream);
+
+/*
+ * ed_apply_H_host -- ed_apply_H on HOST arrays x, y (dim elements of dtype): copies x
+ * to device staging buffers owned by the basis, runs the product, copies y back.
+ * Synchronous.  Not safe to call concurrently on the same basis.
+ */
+int ed_apply_H_host(ed_basis *basis, const double *J, const double *Jz, const void *x_host,
+                    void *y_host, int32_t dtype, void *stream);
+
+/* Lanczos options; zero-initialise and set what you need. */
+typedef struct {
+  int32_t max_steps;          /* default 300 when 0 */
+  int32_t fixed_steps;        /* > 0: run exactly this many steps, no convergence test */
+  double tol;                 /* stop when the lowest Ritz value moves by < tol*max(1,|E0|);
+                                 default 1e-13 when 0 */
+  int32_t dtype;              /* ED_F64 or ED_F32 vectors; alpha, beta and the tridiagonal
+                                 eigenproblem are always double */
+  int32_t reserved0;
+  uint64_t seed;              /* start vector x(s) = uniform[-1,1) from SplitMix64 of
+                                 (s + (2 seed + 1) * 0x9E3779B97F4A7C15), unless v0 given */
+  const void *v0;             /* optional DEVICE start vector (dtype, dim) */
+  void *psi;                  /* optional DEVICE output (dtype, dim): normalised ground
+                                 state from a second Lanczos pass */
+  double *alpha;              /* optional HOST output [max_steps] */
+  double *beta;               /* optional HOST output [max_steps] */
+  void *stream;
+} ed_lanczos_opts;
+
+typedef struct {
+  double E0;                  /* lowest Ritz value */
+  int32_t steps;              /* Lanczos steps taken */
+  int32_t converged;          /* 1 when the tolerance was met (or breakdown: invariant
+                                 subspace found) */
+  double rq;                  /* <psi|H|psi> with fp64 accumulation when psi was
+                                 requested (Rayleigh quotient), else 0 */
+  double ms_total;            /* wall time */
+  double ms_apply;            /* device time spent in apply_H (CUDA events) */
+} ed_lanczos_result;
+
+/*
+ * ed_lanczos -- ground-state energy by the Lanczos iteration with apply_H as the
+ * matrix-vector product (Sec. IV: the product dominates; dots, scalings and the
+ * tridiagonal eigenproblem are cheap).  Three device vectors of dtype (four with psi);
+ * alpha = <v, Hv> and beta = ||w|| reduced in double per block then summed on the
+ * host in a fixed order; lowest eigenvalue of the tridiagonal matrix by Sturm-sequence
+ * bisection in double.  Synchronous.
+ * Errors: ED_ERR_EMPTY (dim 0), ED_ERR_INVALID, ED_ERR_OOM, ED_ERR_CUDA.
+ */
+int ed_lanczos(ed_basis *basis, const double *J, const double *Jz, const ed_lanczos_opts *opts,
+               ed_lanczos_result *result);
+
+/*
+ * ed_dot -- sum_i conj(x_i) y_i over dim DEVICE elements of dtype, in double, written to
+ * the HOST array out[2] = (re, im).  Synchronous.  Scratch lives in the basis.
+ */
+int ed_dot(ed_basis *basis, const void *x, const void *y, int32_t dtype, double *out, void *stream);
+
+/* ed_last_error -- message of the last failing call on this thread ("" if none). */
+const char *ed_last_error(void);
+
+/* ed_version -- library version string. */
+const char *ed_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCED_H */

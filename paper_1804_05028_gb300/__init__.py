@@ -1,0 +1,317 @@
+"""Python binding of libsced (include/sced.h): argument marshalling only.
+
+Every step of the symmetry-adapted product runs in the CUDA library; this module
+turns numpy arrays and torch CUDA tensors into the plain pointers and sizes of the
+C ABI.  There is no fallback: if ``libsced.so`` is missing or cannot be loaded the
+import of :func:`lib` raises.
+
+The names follow the C ABI: :func:`build_basis`, :meth:`Basis.apply_H`,
+:meth:`Basis.lanczos`, :meth:`Basis.find_rep`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["lib", "build", "build_basis", "Basis", "EdError", "F64", "F32", "C128", "C64",
+           "LIB_PATH", "SYMBOLS"]
+
+F64, F32, C128, C64 = 0, 1, 2, 3
+LIB_PATH = _build.LIB
+# every function declared in include/sced.h
+SYMBOLS = ["ed_build_basis", "ed_free_basis", "ed_basis_info", "ed_basis_export",
+           "ed_find_rep", "ed_apply_H", "ed_apply_H_rows", "ed_apply_H_host", "ed_lanczos",
+           "ed_dot", "ed_last_error", "ed_version"]
+
+_ERR = {1: "ED_ERR_INVALID", 2: "ED_ERR_UNSTABLE", 3: "ED_ERR_OOM", 4: "ED_ERR_CUDA",
+        5: "ED_ERR_TIMEOUT", 6: "ED_ERR_EMPTY", 7: "ED_ERR_UNSUPPORTED"}
+
+
+class EdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Lattice(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int32), ("n_sublat", ctypes.c_int32),
+                ("n_bonds", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("bonds", ctypes.c_void_p), ("bond_class", ctypes.c_void_p)]
+
+
+class _Group(ctypes.Structure):
+    _fields_ = [("n_sym", ctypes.c_int32), ("perm", ctypes.c_void_p)]
+
+
+class _Irrep(ctypes.Structure):
+    _fields_ = [("phase_denom", ctypes.c_int32), ("phase_num", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("bucket_target", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int64), ("is_real", ctypes.c_int32),
+                ("n_sites", ctypes.c_int32), ("n_sublat", ctypes.c_int32),
+                ("n_sym", ctypes.c_int32), ("n_up", ctypes.c_int32),
+                ("n_bonds", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("prefix_rank_bits", ctypes.c_int32), ("prefix_raw_bits", ctypes.c_int32),
+                ("postfix_bits", ctypes.c_int32), ("n_keys", ctypes.c_int64),
+                ("max_bucket", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
+                ("index_bytes", ctypes.c_int64), ("basis_bytes", ctypes.c_int64),
+                ("sym_list_len", ctypes.c_int64), ("build_ms", ctypes.c_double)]
+
+
+class _LOpts(ctypes.Structure):
+    _fields_ = [("max_steps", ctypes.c_int32), ("fixed_steps", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("dtype", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("v0", ctypes.c_void_p), ("psi", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p)]
+
+
+class _LRes(ctypes.Structure):
+    _fields_ = [("E0", ctypes.c_double), ("steps", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("rq", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_apply", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libsced.so for sm_103a in-tree."""
+    return _build.build(force=force, verbose=verbose)
+
+
+def lib():
+    """Load libsced.so (raises when it is missing: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libsced.so not built ({LIB_PATH}); run "
+                                  "python -c 'import __graft_entry__ as g; g.build()'")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            L.ed_build_basis.argtypes = [vp, vp, vp, i32, vp, vp, ctypes.POINTER(vp)]
+            L.ed_free_basis.argtypes = [vp]
+            L.ed_free_basis.restype = None
+            L.ed_basis_info.argtypes = [vp, vp]
+            L.ed_basis_export.argtypes = [vp, vp, vp]
+            L.ed_find_rep.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
+            L.ed_apply_H.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+            L.ed_apply_H_rows.argtypes = [vp, vp, vp, vp, vp, i32, i64, i64, vp]
+            L.ed_apply_H_host.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+            L.ed_lanczos.argtypes = [vp, vp, vp, vp, vp]
+            L.ed_dot.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.ed_last_error.restype = ctypes.c_char_p
+            L.ed_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise EdError(rc, lib().ed_last_error().decode())
+
+
+def _dtype_code(t) -> int:
+    import torch
+    m = {torch.float64: F64, torch.float32: F32, torch.complex128: C128, torch.complex64: C64}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _np_dtype_code(a) -> int:
+    m = {np.dtype(np.float64): F64, np.dtype(np.float32): F32,
+         np.dtype(np.complex128): C128, np.dtype(np.complex64): C64}
+    if a.dtype not in m:
+        raise TypeError(f"unsupported dtype {a.dtype}")
+    return m[a.dtype]
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype=None):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Basis:
+    """A symmetry sector's basis and lookup tables on the current CUDA device."""
+
+    def __init__(self, handle, J, Jz, n_classes):
+        self._h = handle
+        self.J = tuple(float(v) for v in J) if J is not None else None
+        self.Jz = tuple(float(v) for v in Jz) if Jz is not None else None
+        self.n_classes = n_classes
+        self._info = None
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h and _lib is not None:
+            _lib.ed_free_basis(h)
+
+    def close(self):
+        if self._h:
+            lib().ed_free_basis(self._h)
+            self._h = None
+
+    def info(self) -> dict:
+        if self._info is None:
+            inf = _Info()
+            _check(lib().ed_basis_info(self._h, ctypes.byref(inf)))
+            self._info = {k: getattr(inf, k) for k, _ in _Info._fields_}
+        return dict(self._info)
+
+    @property
+    def dim(self) -> int:
+        return int(self.info()["dim"])
+
+    @property
+    def is_real(self) -> bool:
+        return bool(self.info()["is_real"])
+
+    def export(self):
+        """(states uint64[D], stab uint16[D]) as numpy arrays."""
+        D = self.dim
+        s = np.empty(D, np.uint64)
+        t = np.empty(D, np.uint16)
+        if D:
+            _check(lib().ed_basis_export(self._h, s.ctypes.data, t.ctypes.data))
+        return s, t
+
+    def _couplings(self, J, Jz):
+        J = self.J if J is None else tuple(float(v) for v in J)
+        Jz = (self.Jz if self.Jz is not None else (1.0,) * len(J)) if Jz is None else tuple(float(v) for v in Jz)
+        if J is None or len(J) != self.n_classes or len(Jz) != self.n_classes:
+            raise ValueError(f"need {self.n_classes} couplings per class")
+        return (ctypes.c_double * len(J))(*J), (ctypes.c_double * len(Jz))(*Jz)
+
+    def find_rep(self, states, stream=None):
+        """Alg. 2 on a uint64 CUDA tensor of configurations: (rep, sym, stab, index)."""
+        import torch
+        n = states.numel()
+        dev = states.device
+        rep = torch.empty(n, dtype=torch.uint64, device=dev)
+        sym = torch.empty(n, dtype=torch.int32, device=dev)
+        stab = torch.empty(n, dtype=torch.int32, device=dev)
+        idx = torch.empty(n, dtype=torch.int64, device=dev)
+        _check(lib().ed_find_rep(self._h, _dev(states, torch.uint64), n, _dev(rep), _dev(sym),
+                                 _dev(stab), _dev(idx), _stream(stream)))
+        return rep, sym, stab, idx
+
+    def apply_H(self, x, y=None, J=None, Jz=None, stream=None):
+        """y = H x for CUDA tensors (float64/float32/complex128/complex64)."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        cJ, cJz = self._couplings(J, Jz)
+        _check(lib().ed_apply_H(self._h, cJ, cJz, _dev(x), _dev(y, x.dtype), _dtype_code(x),
+                                _stream(stream)))
+        return y
+
+    def apply_H_rows(self, x, row_begin, row_end, y=None, J=None, Jz=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty(row_end - row_begin, dtype=x.dtype, device=x.device)
+        cJ, cJz = self._couplings(J, Jz)
+        _check(lib().ed_apply_H_rows(self._h, cJ, cJz, _dev(x), _dev(y, x.dtype), _dtype_code(x),
+                                     int(row_begin), int(row_end), _stream(stream)))
+        return y
+
+    def apply_H_host(self, x, y=None, J=None, Jz=None, stream=None):
+        """y = H x for HOST numpy arrays (or pinned CPU tensors); copies inside the call."""
+        if hasattr(x, "data_ptr"):
+            import torch
+            if y is None:
+                y = torch.empty_like(x)
+            code = _dtype_code(x)
+            px, py = ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())
+        else:
+            x = np.ascontiguousarray(x)
+            if y is None:
+                y = np.empty_like(x)
+            code = _np_dtype_code(x)
+            px, py = ctypes.c_void_p(x.ctypes.data), ctypes.c_void_p(y.ctypes.data)
+        cJ, cJz = self._couplings(J, Jz)
+        _check(lib().ed_apply_H_host(self._h, cJ, cJz, px, py, code, _stream(stream)))
+        return y
+
+    def dot(self, x, y, stream=None) -> complex:
+        out = (ctypes.c_double * 2)()
+        _check(lib().ed_dot(self._h, _dev(x), _dev(y, x.dtype), _dtype_code(x), out, _stream(stream)))
+        return complex(out[0], out[1]) if x.is_complex() else out[0]
+
+    def lanczos(self, J=None, Jz=None, dtype=None, max_steps=300, fixed_steps=0, tol=1e-13,
+                seed=1805, v0=None, psi=None, stream=None):
+        """Lanczos ground-state energy; returns a dict (E0, steps, converged, alpha, beta, ...)."""
+        import torch
+        if dtype is None:
+            dtype = torch.float64 if self.is_real else torch.complex128
+        code = {torch.float64: F64, torch.float32: F32, torch.complex128: C128,
+                torch.complex64: C64}[dtype]
+        m = fixed_steps if fixed_steps > 0 else max_steps
+        alpha = np.zeros(m)
+        beta = np.zeros(m)
+        o = _LOpts()
+        o.max_steps, o.fixed_steps, o.tol, o.dtype, o.seed = int(max_steps), int(fixed_steps), float(tol), code, int(seed)
+        o.v0 = _dev(v0, dtype).value if v0 is not None else None
+        o.psi = _dev(psi, dtype).value if psi is not None else None
+        o.alpha, o.beta = alpha.ctypes.data, beta.ctypes.data
+        o.stream = _stream(stream).value
+        r = _LRes()
+        cJ, cJz = self._couplings(J, Jz)
+        _check(lib().ed_lanczos(self._h, cJ, cJz, ctypes.byref(o), ctypes.byref(r)))
+        k = r.steps
+        return {"E0": r.E0, "steps": k, "converged": bool(r.converged), "rq": r.rq,
+                "alpha": alpha[:k].copy(), "beta": beta[:max(k - 1, 0)].copy(),
+                "ms_total": r.ms_total, "ms_apply": r.ms_apply}
+
+
+def build_basis(n_sites, n_sublat, bonds, bond_class, n_classes, perm, phase_num, phase_denom,
+                n_up, J=None, Jz=None, bucket_target=None, stream=None) -> Basis:
+    """Validate a sector, build the sublattice tables and the basis on the current device."""
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32)
+    bcls = np.ascontiguousarray(bond_class, dtype=np.int32)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    pnum = np.ascontiguousarray(phase_num, dtype=np.int32)
+    L = _Lattice(int(n_sites), int(n_sublat), int(bonds.shape[0]), int(n_classes),
+                 bonds.ctypes.data, bcls.ctypes.data)
+    G = _Group(int(perm.shape[0]), perm.ctypes.data)
+    R = _Irrep(int(phase_denom), pnum.ctypes.data)
+    opts = _Opts()
+    opts.bucket_target = int(bucket_target or 0)
+    h = ctypes.c_void_p()
+    _check(lib().ed_build_basis(ctypes.byref(L), ctypes.byref(G), ctypes.byref(R), int(n_up),
+                                ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+    return Basis(h, J, Jz, int(n_classes))
+
+
+def build_basis_from(problem, **kw) -> Basis:
+    """build_basis from an object with the fields of a problem descriptor."""
+    p = problem
+    return build_basis(p.n_sites, p.n_sublat, p.bonds, p.bond_class, p.n_classes, p.perm,
+                       p.phase_num, p.phase_denom, p.n_up, J=p.J, Jz=p.Jz, **kw)

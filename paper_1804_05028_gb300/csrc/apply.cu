@@ -1,0 +1,422 @@
+// apply.cu -- the matrix-free product y = H x on the symmetry-adapted basis
+// (Sec. IV, Eqs. 12-17 of arXiv:1804.05028, restated as a row-wise pull), the
+// find_rep test hook, and the streaming vector kernels of the Lanczos iteration.
+//
+// Row-wise pull: row i owns y_i.  For every antiparallel bond of its representative
+// s_i the exchanged configuration s' is mapped to its representative s_j = h s' by
+// sublattice coding (Alg. 2), s_j is located in Basis through Limits (Sec. IV), and
+// y_i += (J_c/2) chi(h) sqrt(|Stab_j|/|Stab_i|) x_j -- the conjugate-transposed form
+// of the push of Alg. 4, exact because H is Hermitian.  Each y_i is written once:
+// no atomics, no inter-block communication, fixed summation order.
+#include "sced_internal.cuh"
+#include <cuda_fp16.h>
+
+namespace {
+
+template <typename V> struct Vt;
+template <> struct Vt<double> { using A = double; static constexpr bool cplx = false; };
+template <> struct Vt<float> { using A = float; static constexpr bool cplx = false; };
+template <> struct Vt<double2> { using A = double; static constexpr bool cplx = true; };
+template <> struct Vt<float2> { using A = float; static constexpr bool cplx = true; };
+
+struct ApplyParams {
+  DevTables T;
+  DevIndex I;
+  int n_classes;
+  int cls_off[ED_MAXCLS + 1];
+  double jh[ED_MAXCLS];    // J_c / 2, amplitude of the exchange term
+  double jzq[ED_MAXCLS];   // J_c Jz_c / 4, S^z S^z of a parallel pair
+  const uint8_t *bond_pos; // [n_bonds][2] bit positions (N-1-label), class-sorted
+  const double *sqrt_tab;  // sqrt(t), t = 0..nsym
+  const double *rsqrt_tab; // 1/sqrt(t)
+  const double *cs;        // [denom][2] cos, sin (complex sectors)
+  const void *x;
+  void *y;
+  int64_t r0, r1;          // rows [r0, r1); y[0] is row r0
+  double *partial;         // optional [gridDim.x] (or 2x for complex) partial <x_rows, y>
+  // shared-memory layout (bytes)
+  int stage_tables;
+  uint32_t sym_list_bytes;
+  uint32_t off_rep, off_symoff, off_phase, off_symlist, off_dest, off_bond, off_sqrt, off_cs;
+  uint32_t smem_bytes;
+};
+
+template <typename A>
+__device__ __forceinline__ void block_reduce_store(A v, double *out, int slot) {
+  __shared__ double red[32];
+  double d = (double)v;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xFFFFFFFFu, d, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = d;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    d = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xFFFFFFFFu, d, o);
+    if (lane == 0) out[slot] = d;
+  }
+}
+
+// Stage Rep_X, Sym_X offsets and lists, dest, phases, bond positions and the norm /
+// character tables in shared memory (they are small: O(nsub 2^n) entries).
+template <typename A, bool kStage>
+__device__ __forceinline__ void stage(const ApplyParams &P, unsigned char *sm) {
+  const DevTables &T = P.T;
+  auto cp32 = [&](uint32_t off, const void *src, size_t bytes) {
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(sm + off);
+    for (size_t k = threadIdx.x; k < bytes / 4; k += blockDim.x) d[k] = s[k];
+  };
+  auto cp8 = [&](uint32_t off, const void *src, size_t bytes) {
+    const unsigned char *s = reinterpret_cast<const unsigned char *>(src);
+    for (size_t k = threadIdx.x; k < bytes; k += blockDim.x) sm[off + k] = s[k];
+  };
+  if (kStage) {
+    const size_t nn = (size_t)1 << T.n;
+    cp32(P.off_rep, T.rep, (size_t)T.nsub * nn * 4);
+    cp32(P.off_symoff, T.sym_off, (size_t)T.nsub * (nn + 1) * 4);
+    cp32(P.off_phase, T.phase, (size_t)T.nsym * 4);
+    cp8(P.off_symlist, T.sym_list, (size_t)P.sym_list_bytes);
+    cp8(P.off_dest, T.dest, (size_t)T.nsym * T.nsub);
+  }
+  cp8(P.off_bond, P.bond_pos, (size_t)P.cls_off[P.n_classes] * 2);
+  A *sq = reinterpret_cast<A *>(sm + P.off_sqrt);
+  for (int k = threadIdx.x; k <= T.nsym; k += blockDim.x) {
+    sq[2 * k] = (A)P.sqrt_tab[k];
+    sq[2 * k + 1] = (A)P.rsqrt_tab[k];
+  }
+  if (P.cs) {
+    A *c = reinterpret_cast<A *>(sm + P.off_cs);
+    for (int k = threadIdx.x; k < 2 * T.denom; k += blockDim.x) c[k] = (A)P.cs[k];
+  }
+  __syncthreads();
+}
+
+template <typename V, bool kStage>
+__global__ void __launch_bounds__(256) apply_h_kernel(const ApplyParams P) {
+  using A = typename Vt<V>::A;
+  constexpr bool kC = Vt<V>::cplx;
+  extern __shared__ __align__(16) unsigned char sm[];
+  stage<A, kStage>(P, sm);
+  const DevTables &T = P.T;
+  const uint32_t *rep_s = kStage ? reinterpret_cast<const uint32_t *>(sm + P.off_rep) : T.rep;
+  const uint32_t *symoff_s =
+      kStage ? reinterpret_cast<const uint32_t *>(sm + P.off_symoff) : T.sym_off;
+  const uint16_t *symlist_s =
+      kStage ? reinterpret_cast<const uint16_t *>(sm + P.off_symlist) : T.sym_list;
+  const uint8_t *dest_s = kStage ? reinterpret_cast<const uint8_t *>(sm + P.off_dest) : T.dest;
+  const int32_t *phase_s =
+      kStage ? reinterpret_cast<const int32_t *>(sm + P.off_phase) : T.phase;
+  const uint8_t *bond_s = sm + P.off_bond;
+  const A *sq = reinterpret_cast<const A *>(sm + P.off_sqrt);
+  const A *cs = reinterpret_cast<const A *>(sm + P.off_cs);
+  const V *x = reinterpret_cast<const V *>(P.x);
+  V *y = reinterpret_cast<V *>(P.y);
+
+  double dot_re = 0.0, dot_im = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = P.r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.r1; i += stride) {
+    const uint64_t s = __ldg(P.I.basis + i);
+    const int ti = __ldg(P.I.stab + i);
+    A row_re = 0, row_im = 0;
+    double diag = 0.0;
+    for (int c = 0; c < P.n_classes; c++) {
+      A acc_re = 0, acc_im = 0;
+      int nanti = 0;
+      const int b1 = P.cls_off[c + 1];
+      for (int b = P.cls_off[c]; b < b1; b++) {
+        const int pa = bond_s[2 * b], pb = bond_s[2 * b + 1];
+        if ((((s >> pa) ^ (s >> pb)) & 1ULL) == 0) continue;
+        nanti++;
+        const uint64_t s2 = s ^ ((1ULL << pa) | (1ULL << pb));
+        const RepOut R = find_rep(T, rep_s, symoff_s, symlist_s, dest_s, phase_s, s2);
+        if (R.mixed) continue;
+        const int64_t j = lookup_index(P.I, R.rep);
+        if (j < 0) continue;
+        const A w = sq[2 * R.t];
+        const int ph = phase_s[R.g];
+        if constexpr (!kC) {
+          const A v = w * x[j];
+          acc_re += (ph == 0) ? v : -v;   // real sector: chi(h) = +1 or -1
+        } else {
+          const V xj = x[j];
+          const A cr = cs[2 * ph] * w, ci = cs[2 * ph + 1] * w;
+          acc_re += cr * xj.x - ci * xj.y;
+          acc_im += cr * xj.y + ci * xj.x;
+        }
+      }
+      diag += P.jzq[c] * (double)((b1 - P.cls_off[c]) - 2 * nanti);
+      row_re += (A)P.jh[c] * acc_re;
+      if constexpr (kC) row_im += (A)P.jh[c] * acc_im;
+    }
+    const A rs = sq[2 * ti + 1];
+    if constexpr (!kC) {
+      const V xi = x[i];
+      const V yi = (A)diag * xi + row_re * rs;
+      y[i - P.r0] = yi;
+      if (P.partial) dot_re += (double)xi * (double)yi;
+    } else {
+      const V xi = x[i];
+      V yi;
+      yi.x = (A)diag * xi.x + row_re * rs;
+      yi.y = (A)diag * xi.y + row_im * rs;
+      y[i - P.r0] = yi;
+      if (P.partial) {
+        dot_re += (double)xi.x * yi.x + (double)xi.y * yi.y;
+        dot_im += (double)xi.x * yi.y - (double)xi.y * yi.x;
+      }
+    }
+  }
+  if (P.partial) {
+    block_reduce_store<double>(dot_re, P.partial, blockIdx.x);
+    if (kC) block_reduce_store<double>(dot_im, P.partial, gridDim.x + blockIdx.x);
+  }
+}
+
+template <typename V, bool kStage>
+int launch_apply_t(const ApplyParams &P, int grid, cudaStream_t st) {
+  auto k = apply_h_kernel<V, kStage>;
+  if (P.smem_bytes > 48 * 1024)
+    ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
+  k<<<grid, 256, P.smem_bytes, st>>>(P);
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+__global__ void find_rep_kernel(const DevTables T, const DevIndex I, const uint64_t *states,
+                                int64_t n, uint64_t *rep, int32_t *sym, int32_t *stab,
+                                int64_t *index) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const RepOut R = find_rep(T, T.rep, T.sym_off, T.sym_list, T.dest, T.phase, states[i]);
+    if (rep) rep[i] = R.rep;
+    if (sym) sym[i] = R.g;
+    if (stab) stab[i] = R.t;
+    if (index) index[i] = (R.mixed || I.D == 0) ? -1 : lookup_index(I, R.rep);
+  }
+}
+
+// ------------------------------ vector kernels -------------------------------------
+template <typename V>
+__global__ void dot_kernel(const V *x, const V *y, int64_t n, double *partial) {
+  double re = 0, im = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (Vt<V>::cplx) {
+      const V a = x[i], b = y[i];
+      re += (double)a.x * b.x + (double)a.y * b.y;
+      im += (double)a.x * b.y - (double)a.y * b.x;
+    } else {
+      re += (double)x[i] * (double)y[i];
+    }
+  }
+  block_reduce_store<double>(re, partial, blockIdx.x);
+  if (Vt<V>::cplx) block_reduce_store<double>(im, partial, gridDim.x + blockIdx.x);
+}
+
+// w <- w - a v - b vprev ; partial ||w||^2   (vprev may be null)
+template <typename V>
+__global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, double b,
+                                 int64_t n, double *partial) {
+  using A = typename Vt<V>::A;
+  double acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (Vt<V>::cplx) {
+      // a and b are real (Hermitian tridiagonal)
+      double wr = (double)w[i].x - a * (double)v[i].x;
+      double wi = (double)w[i].y - a * (double)v[i].y;
+      if (vprev) { wr -= b * (double)vprev[i].x; wi -= b * (double)vprev[i].y; }
+      V o; o.x = (A)wr; o.y = (A)wi;
+      w[i] = o;
+      acc += (double)o.x * o.x + (double)o.y * o.y;
+    } else {
+      double t = (double)w[i] - a * (double)v[i];
+      if (vprev) t -= b * (double)vprev[i];
+      const A o = (A)t;
+      w[i] = o;
+      acc += (double)o * (double)o;
+    }
+  }
+  block_reduce_store<double>(acc, partial, blockIdx.x);
+}
+
+template <typename V>
+__global__ void scale_kernel(V *v, double s, int64_t n) {
+  using A = typename Vt<V>::A;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (Vt<V>::cplx) { V o = v[i]; o.x = (A)(o.x * s); o.y = (A)(o.y * s); v[i] = o; }
+    else v[i] = (A)((double)v[i] * s);
+  }
+}
+
+template <typename V>
+__global__ void axpy_kernel(V *y, const V *x, double a, int64_t n) {
+  using A = typename Vt<V>::A;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (Vt<V>::cplx) {
+      V o = y[i]; o.x = (A)(o.x + a * x[i].x); o.y = (A)(o.y + a * x[i].y); y[i] = o;
+    } else y[i] = (A)((double)y[i] + a * (double)x[i]);
+  }
+}
+
+// start vector v_i = uniform[-1, 1) keyed by the basis state (real part; imaginary part
+// from a second stream for complex types)
+template <typename V>
+__global__ void start_kernel(V *v, const uint64_t *basis, int64_t n, uint64_t seed) {
+  using A = typename Vt<V>::A;
+  const uint64_t off0 = (seed * 2 + 1) * 0x9E3779B97F4A7C15ULL;
+  const uint64_t off1 = (seed * 2 + 2) * 0x9E3779B97F4A7C15ULL;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = basis[i];
+    const double u0 = (double)(splitmix64_mix(s + off0) >> 11) * (1.0 / 9007199254740992.0);
+    if constexpr (Vt<V>::cplx) {
+      const double u1 = (double)(splitmix64_mix(s + off1) >> 11) * (1.0 / 9007199254740992.0);
+      V o; o.x = (A)(2.0 * u0 - 1.0); o.y = (A)(2.0 * u1 - 1.0); v[i] = o;
+    } else {
+      v[i] = (A)(2.0 * u0 - 1.0);
+    }
+  }
+}
+
+int grid_for(const ed_basis *B, int64_t n, int per_sm) {
+  int64_t g = (int64_t)B->sm_count * per_sm;
+  int64_t need = (n + 255) / 256;
+  if (need < g) g = need;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// --------------------------------- launchers ---------------------------------------
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const void *x,
+                    void *y, int dtype, int64_t r0, int64_t r1, double *partial,
+                    cudaStream_t st) {
+  if (r1 <= r0) return ED_OK;
+  ApplyParams P{};
+  P.T = B->T;
+  P.I = B->I;
+  P.n_classes = B->n_classes;
+  for (int c = 0; c <= B->n_classes; c++) P.cls_off[c] = B->cls_off[c];
+  for (int c = 0; c < B->n_classes; c++) {
+    P.jh[c] = 0.5 * J[c];
+    P.jzq[c] = 0.25 * J[c] * Jz[c];
+  }
+  P.bond_pos = B->d_bond_pos;
+  P.sqrt_tab = B->d_sqrt;
+  P.rsqrt_tab = B->d_rsqrt;
+  const bool cplx = (dtype == ED_C128 || dtype == ED_C64);
+  P.cs = cplx ? B->d_cs : nullptr;
+  P.x = x;
+  P.y = y;
+  P.r0 = r0;
+  P.r1 = r1;
+  P.partial = partial;
+  // shared-memory layout
+  const size_t nn = (size_t)1 << B->n;
+  const size_t abytes = (dtype == ED_F64 || dtype == ED_C128) ? 8 : 4;
+  size_t off = 0;
+  const size_t tab_bytes = align16((size_t)B->nsub * nn * 4) +
+                           align16((size_t)B->nsub * (nn + 1) * 4) +
+                           align16((size_t)B->nsym * 4) + align16(B->sym_list_len * 2) +
+                           align16((size_t)B->nsym * B->nsub);
+  const size_t rest = align16((size_t)B->n_bonds * 2) + align16((size_t)(B->nsym + 1) * 2 * abytes) +
+                      align16((size_t)B->denom * 2 * abytes);
+  const size_t kMaxSmem = 200 * 1024;
+  P.stage_tables = (tab_bytes + rest <= kMaxSmem) ? 1 : 0;
+  P.sym_list_bytes = (uint32_t)(B->sym_list_len * 2);
+  if (P.stage_tables) {
+    P.off_rep = (uint32_t)off; off += align16((size_t)B->nsub * nn * 4);
+    P.off_symoff = (uint32_t)off; off += align16((size_t)B->nsub * (nn + 1) * 4);
+    P.off_phase = (uint32_t)off; off += align16((size_t)B->nsym * 4);
+    P.off_symlist = (uint32_t)off; off += align16(B->sym_list_len * 2);
+    P.off_dest = (uint32_t)off; off += align16((size_t)B->nsym * B->nsub);
+  } else {
+    P.off_symlist = P.off_dest = 0;
+  }
+  P.off_bond = (uint32_t)off; off += align16((size_t)B->n_bonds * 2);
+  P.off_sqrt = (uint32_t)off; off += align16((size_t)(B->nsym + 1) * 2 * abytes);
+  P.off_cs = (uint32_t)off; off += align16((size_t)B->denom * 2 * abytes);
+  P.smem_bytes = (uint32_t)off;
+  // fixed grid: a whole number of CTAs per SM, grid-stride over rows
+  const int grid = grid_for(B, r1 - r0, 8);
+  if (partial && grid > B->n_partial / 2) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
+  const bool sg = P.stage_tables != 0;
+  switch (dtype) {
+    case ED_F64: return sg ? launch_apply_t<double, true>(P, grid, st) : launch_apply_t<double, false>(P, grid, st);
+    case ED_F32: return sg ? launch_apply_t<float, true>(P, grid, st) : launch_apply_t<float, false>(P, grid, st);
+    case ED_C128: return sg ? launch_apply_t<double2, true>(P, grid, st) : launch_apply_t<double2, false>(P, grid, st);
+    case ED_C64: return sg ? launch_apply_t<float2, true>(P, grid, st) : launch_apply_t<float2, false>(P, grid, st);
+  }
+  return ed_fail(ED_ERR_INVALID, "unknown dtype");
+}
+
+int ed_apply_grid(const ed_basis *B, int64_t rows) { return grid_for(B, rows, 8); }
+
+int ed_launch_find_rep(const ed_basis *B, const uint64_t *states, int64_t n, uint64_t *rep,
+                       int32_t *sym, int32_t *stab, int64_t *index, cudaStream_t st) {
+  if (n <= 0) return ED_OK;
+  const int grid = grid_for(B, n, 8);
+  find_rep_kernel<<<grid, 256, 0, st>>>(B->T, B->I, states, n, rep, sym, stab, index);
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+#define ED_DISPATCH(dtype, CALL)                                 \
+  switch (dtype) {                                               \
+    case ED_F64: { using V = double; CALL; break; }              \
+    case ED_F32: { using V = float; CALL; break; }               \
+    case ED_C128: { using V = double2; CALL; break; }            \
+    case ED_C64: { using V = float2; CALL; break; }              \
+    default: return ed_fail(ED_ERR_INVALID, "unknown dtype");    \
+  }
+
+int ed_launch_dot(const ed_basis *B, const void *x, const void *y, int dtype, double *partial,
+                  int nblk, cudaStream_t st) {
+  ED_DISPATCH(dtype, (dot_kernel<V><<<nblk, 256, 0, st>>>((const V *)x, (const V *)y, B->D, partial)));
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+int ed_launch_axpy_norm(const ed_basis *B, void *w, const void *v, const void *vprev, double a,
+                        double b, int dtype, double *partial, int nblk, cudaStream_t st) {
+  ED_DISPATCH(dtype, (axpy_norm_kernel<V><<<nblk, 256, 0, st>>>((V *)w, (const V *)v,
+                                                                (const V *)vprev, a, b, B->D,
+                                                                partial)));
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+int ed_launch_scale(const ed_basis *B, void *v, double s, int dtype, cudaStream_t st) {
+  const int grid = grid_for(B, B->D, 8);
+  ED_DISPATCH(dtype, (scale_kernel<V><<<grid, 256, 0, st>>>((V *)v, s, B->D)));
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+int ed_launch_axpy(const ed_basis *B, void *y, const void *x, double a, int dtype,
+                   cudaStream_t st) {
+  const int grid = grid_for(B, B->D, 8);
+  ED_DISPATCH(dtype, (axpy_kernel<V><<<grid, 256, 0, st>>>((V *)y, (const V *)x, a, B->D)));
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+int ed_launch_start(const ed_basis *B, void *v, uint64_t seed, int dtype, cudaStream_t st) {
+  const int grid = grid_for(B, B->D, 8);
+  ED_DISPATCH(dtype, (start_kernel<V><<<grid, 256, 0, st>>>((V *)v, B->d_basis, B->D, seed)));
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+int ed_launch_copy(const ed_basis *B, void *dst, const void *src, int dtype, cudaStream_t st) {
+  const size_t es = (dtype == ED_F64) ? 8 : (dtype == ED_F32) ? 4 : (dtype == ED_C128) ? 16 : 8;
+  ED_CK(cudaMemcpyAsync(dst, src, es * (size_t)B->D, cudaMemcpyDeviceToDevice, st));
+  return ED_OK;
+}
