@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Throughput of the symmetry-adapted matrix-free H x inside Lanczos on GB300.
+
+A step is one Lanczos iteration on the sector: the row-pull product y = H v
+(representative search by sublattice coding, Limits lookup, gather) with the fused
+<v, Hv> partials, the three-term update with the ||w|| partials, and the scaling of
+the next vector.  Both precisions are timed on the same sector and start vector:
+fp64 vectors, and fp32 vectors with fp64 alpha/beta and tridiagonal solve ("mixed").
+The headline is the mixed form when its ground-state energy agrees with the fp64
+one to |dE0/E0| <= 1e-9, else the fp64 form.
+
+Metric: symmetrised H x nonzeros per second = (D diagonal terms + off-diagonal terms
+whose target survives the projection) per product x products per second, summed over
+ranks (each rank runs its own replica of the sector; weak scaling).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       (N > 1: launched by torch.distributed.run, one rank per GPU)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "Symmetrized H·v nonzeros/s + HBM roofline %, mixed vs FP64 at |ΔE0/E0|≤1e-9"
+UNIT = "nonzeros/s"
+WORKLOADS = {
+    "square36": ("J1-J2 Heisenberg 6x6 torus, J1=1 J2=0.5, Sz=0, 36 translations x C4v "
+                 "(288), Gamma-A1", lambda: workloads.config_square36(0.5)),
+    "tilted40": ("Heisenberg J1 40-site tilted square (6,2),(-2,6), Sz=0, 40 translations x "
+                 "C4 (160), Gamma-A", workloads.config_tilted40),
+    "chain16": ("Heisenberg chain N=16 periodic, Sz=0, C16, k=0", workloads.config_chain16),
+}
+KERNEL_SOURCES = ["paper_1804_05028_gb300/csrc/apply.cu",
+                  "paper_1804_05028_gb300/csrc/sced_internal.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, dtype: str):
+    """DRAM bytes per apply_h launch from the committed ncu summary, if the kernel source
+    has not changed since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", f"apply_h_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(rf"traffic_bytes_per_launch\[{dtype}\]:\s*([0-9]+)\s+source_sha:\s*([0-9a-f]+)", txt)
+    if not m or m.group(2) != kernel_hash():
+        return None
+    return int(m.group(1))
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def alg_bytes(D: int, n_off: int, vec_bytes: int) -> int:
+    """Bytes the method must move per product: per row the state (8), |Stab| (2), x_i and
+    y_i; per off-diagonal term one gathered x_j."""
+    return D * (8 + 2 + 2 * vec_bytes) + n_off * vec_bytes
+
+
+def cpu_baseline(p, states, seconds: float, seed: int = 7):
+    """The oracle's matrix-free rows (brute-force representatives) on a sample of rows."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    xf = lambda q: workloads.state_uniform(q, 1804)
+    n = 64
+    oracle.rows(p, states[:16], xf)
+    t0 = time.perf_counter()
+    oracle.rows(p, states[np.sort(rng.choice(states.size, n, replace=False))], xf)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(states.size, max(64, n * seconds / dt)))
+    pick = np.sort(rng.choice(states.size, n, replace=False))
+    diag, nt, reps, val = oracle.columns(p, states[pick[:1]])   # warm the library
+    t0 = time.perf_counter()
+    oracle.rows(p, states[pick], xf)
+    dt = time.perf_counter() - t0
+    _, nt, _, _ = oracle.columns(p, states[pick])
+    nnz = int(n + nt.sum())
+    return {"value": nnz / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{n} rows of {states.size} (matrix-free brute-force rows, fp64), {nnz} nonzeros in {dt:.1f}s"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle as it stands, on the host cores, same metric and config."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    desc, mk = WORKLOADS[args.workload]
+    p = mk()
+    # representatives of the sector from the oracle itself: sample configurations and
+    # keep their representatives (the oracle cannot enumerate C(36,18) states)
+    rng = np.random.default_rng(11)
+    N, n_up = p.n_sites, p.n_up
+    cfg = np.zeros(4096, np.uint64)
+    for i in range(cfg.size):
+        cfg[i] = np.bitwise_or.reduce(np.uint64(1) << rng.choice(N, n_up, replace=False).astype(np.uint64))
+    rep, _, _, kept = oracle.representatives(p, cfg)
+    reps = np.unique(rep[kept])
+    xf = lambda q: workloads.state_uniform(q, 1804)
+    # calibrate rows per step to about one second
+    oracle.rows(p, reps[:16], xf)
+    t0 = time.perf_counter()
+    oracle.rows(p, reps[:64], xf)
+    per_row = max((time.perf_counter() - t0) / 64, 1e-6)
+    n_rows = int(max(16, min(reps.size, 1.0 / per_row)))
+    step_rows = [reps[np.sort(rng.choice(reps.size, n_rows, replace=False))] for _ in range(args.warmup + args.steps)]
+    for k in range(args.warmup):
+        oracle.rows(p, step_rows[k], xf)
+    nnz = 0
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        oracle.rows(p, step_rows[k], xf)
+    dt = time.perf_counter() - t0
+    for k in range(args.warmup, args.warmup + args.steps):
+        _, nt, _, _ = oracle.columns(p, step_rows[k])
+        nnz += int(nt.sum()) + step_rows[k].size
+    value = nnz / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (state-keyed uniform[-1,1) vectors, seed 1804)",
+            "config": {"workload": args.workload, "description": desc, "rows_per_step": n_rows},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{n_rows} sampled representative rows per step, matrix-free brute force"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="square36", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1804_05028_gb300 as ed
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def allmax(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    desc, mk = WORKLOADS[args.workload]
+    p = mk()
+    ed.build()
+    B = ed.build_basis_from(p)
+    info = B.info()
+    D = info["dim"]
+    n_flip, n_off = B.count_terms()
+    nnz = D + n_off
+
+    # accuracy of the mixed form against fp64 (untimed): full Lanczos runs to convergence
+    acc = {}
+    if not args.no_accuracy:
+        r64 = B.lanczos(dtype=torch.float64, max_steps=400)
+        psi32 = torch.empty(D, dtype=torch.float32, device="cuda")
+        r32 = B.lanczos(dtype=torch.float32, max_steps=400, psi=psi32)
+        acc = {"E0_f64": r64["E0"], "steps_f64": r64["steps"], "E0_mixed": r32["E0"],
+               "steps_mixed": r32["steps"], "rq_mixed": r32["rq"],
+               "dE0_rel_mixed": abs(r32["E0"] - r64["E0"]) / abs(r64["E0"]),
+               "dE0_rel_mixed_rq": abs(r32["rq"] - r64["E0"]) / abs(r64["E0"])}
+        del psi32
+
+    pk, pk_kind = peaks()
+    results = {}
+    for name, dt, vb in (("f64", torch.float64, 8), ("mixed", torch.float32, 4)):
+        work = torch.empty(3 * D, dtype=dt, device="cuda")
+        B.lanczos(dtype=dt, fixed_steps=max(args.warmup, 1), work=work)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as cs:
+            e0.record()
+            r = B.lanczos(dtype=dt, fixed_steps=args.steps, work=work)
+            e1.record()
+            torch.cuda.synchronize()
+        barrier()
+        ms = allmax(e0.elapsed_time(e1))
+        apply_ms = r["ms_apply"] / args.steps
+        ab = alg_bytes(D, n_off, vb)
+        achieved = ab / (apply_ms * 1e-3) / 1e9
+        results[name] = {
+            "value": world * nnz * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "apply_ms": apply_ms, "clocks": cs.summary(),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
+                         "traffic": profiled_traffic(args.workload, name),
+                         "alg_bytes_per_launch": ab},
+            "gpu_launches": 3 * args.steps + 2,
+        }
+        del work
+
+    ok_mixed = (not acc) or acc["dE0_rel_mixed"] <= 1e-9
+    head = results["mixed"] if ok_mixed else results["f64"]
+    head_name = "mixed" if ok_mixed else "f64"
+
+    # end to end through the host-buffer entry point: H2D of x, product, D2H of y per step
+    e2e = None
+    if rank == 0 or world > 1:
+        hd = torch.float32 if ok_mixed else torch.float64
+        xh = torch.from_numpy(workloads.state_uniform(B.export()[0], 1804)).to(hd).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        for _ in range(max(args.warmup, 1)):
+            B.apply_H_host(xh, yh)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            B.apply_H_host(xh, yh)
+        torch.cuda.synchronize()
+        t_e2e = allmax(time.perf_counter() - t0)
+        eb = xh.numel() * xh.element_size()
+        e2e = {"value": world * nnz * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": eb,
+               "d2h_bytes_per_step": eb, "ms_per_step": 1000 * t_e2e / args.steps,
+               "what": "ed_apply_H_host: pinned host x -> device, product, device -> pinned host y"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, B.export()[0], args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 vectors / f64 scalars" if head_name == "mixed" else "f64",
+            "data": "synthetic (state-keyed uniform[-1,1) start vector, seed 1805)",
+            "config": {"workload": args.workload, "description": desc, "dim": D,
+                       "offdiag_terms_per_product": n_off, "exchange_terms_per_product": n_flip,
+                       "nonzeros_per_product": nnz, "n_sublat": p.n_sublat, "n_sym": p.n_sym,
+                       "step": "one Lanczos iteration (apply_H with fused <v,Hv>, update with ||w||, scale)",
+                       "l2": "inputs larger than L2: basis %d MB, each vector %d MB" % (D * 8 >> 20, D * (4 if head_name == 'mixed' else 8) >> 20),
+                       "index": {k: info[k] for k in ("prefix_rank_bits", "prefix_raw_bits", "postfix_bits", "n_keys", "max_bucket")},
+                       "parallelism": f"replicas x{world}"},
+            "roofline": head["roofline"], "clocks": head["clocks"], "gpu_launches": head["gpu_launches"],
+            "e2e": e2e, "cpu_baseline": cpu, "headline": head_name,
+            "fp64": results["f64"], "mixed": results["mixed"], "accuracy": acc,
+            "kernel_sha": kernel_hash(),
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -192,6 +192,9 @@ typedef struct {
   double *alpha;              /* optional HOST output [max_steps] */
   double *beta;               /* optional HOST output [max_steps] */
   void *stream;
+  void *work;                 /* optional DEVICE workspace of >= 3 * dim elements of dtype,
+                                 caller-owned; when NULL the call allocates its own */
+  int64_t work_bytes;         /* size of work in bytes */
 } ed_lanczos_opts;
 
 typedef struct {
@@ -222,6 +225,14 @@ int ed_lanczos(ed_basis *basis, const double *J, const double *Jz, const ed_lanc
  * the HOST array out[2] = (re, im).  Synchronous.  Scratch lives in the basis.
  */
 int ed_dot(ed_basis *basis, const void *x, const void *y, int32_t dtype, double *out, void *stream);
+
+/*
+ * ed_count_terms -- how many exchange terms one product generates: *n_flip counts every
+ * (row, antiparallel bond) pair (Eq. 16 applied to every basis state), *n_offdiag those
+ * whose exchanged configuration has a surviving representative, i.e. the off-diagonal
+ * contributions that apply_H gathers.  HOST outputs; synchronous.
+ */
+int ed_count_terms(const ed_basis *basis, int64_t *n_flip, int64_t *n_offdiag, void *stream);
 
 /* ed_last_error -- message of the last failing call on this thread ("" if none). */
 const char *ed_last_error(void);

@@ -26,7 +26,7 @@ LIB_PATH = _build.LIB
 # every function declared in include/sced.h
 SYMBOLS = ["ed_build_basis", "ed_free_basis", "ed_basis_info", "ed_basis_export",
            "ed_find_rep", "ed_apply_H", "ed_apply_H_rows", "ed_apply_H_host", "ed_lanczos",
-           "ed_dot", "ed_last_error", "ed_version"]
+           "ed_dot", "ed_count_terms", "ed_last_error", "ed_version"]
 
 _ERR = {1: "ED_ERR_INVALID", 2: "ED_ERR_UNSTABLE", 3: "ED_ERR_OOM", 4: "ED_ERR_CUDA",
         5: "ED_ERR_TIMEOUT", 6: "ED_ERR_EMPTY", 7: "ED_ERR_UNSUPPORTED"}
@@ -74,7 +74,8 @@ class _LOpts(ctypes.Structure):
                 ("reserved0", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("v0", ctypes.c_void_p), ("psi", ctypes.c_void_p),
                 ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("work", ctypes.c_void_p),
+                ("work_bytes", ctypes.c_int64)]
 
 
 class _LRes(ctypes.Structure):
@@ -113,6 +114,7 @@ def lib():
             L.ed_apply_H_host.argtypes = [vp, vp, vp, vp, vp, i32, vp]
             L.ed_lanczos.argtypes = [vp, vp, vp, vp, vp]
             L.ed_dot.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.ed_count_terms.argtypes = [vp, vp, vp, vp]
             L.ed_last_error.restype = ctypes.c_char_p
             L.ed_version.restype = ctypes.c_char_p
             _lib = L
@@ -260,13 +262,19 @@ class Basis:
         _check(lib().ed_apply_H_host(self._h, cJ, cJz, px, py, code, _stream(stream)))
         return y
 
+    def count_terms(self, stream=None):
+        """(exchange terms generated, those with a surviving target) of one product."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ed_count_terms(self._h, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+        return a.value, b.value
+
     def dot(self, x, y, stream=None) -> complex:
         out = (ctypes.c_double * 2)()
         _check(lib().ed_dot(self._h, _dev(x), _dev(y, x.dtype), _dtype_code(x), out, _stream(stream)))
         return complex(out[0], out[1]) if x.is_complex() else out[0]
 
     def lanczos(self, J=None, Jz=None, dtype=None, max_steps=300, fixed_steps=0, tol=1e-13,
-                seed=1805, v0=None, psi=None, stream=None):
+                seed=1805, v0=None, psi=None, work=None, stream=None):
         """Lanczos ground-state energy; returns a dict (E0, steps, converged, alpha, beta, ...)."""
         import torch
         if dtype is None:
@@ -282,6 +290,9 @@ class Basis:
         o.psi = _dev(psi, dtype).value if psi is not None else None
         o.alpha, o.beta = alpha.ctypes.data, beta.ctypes.data
         o.stream = _stream(stream).value
+        if work is not None:
+            o.work = _dev(work).value
+            o.work_bytes = work.numel() * work.element_size()
         r = _LRes()
         cJ, cJz = self._couplings(J, Jz)
         _check(lib().ed_lanczos(self._h, cJ, cJz, ctypes.byref(o), ctypes.byref(r)))

@@ -197,6 +197,30 @@ __global__ void find_rep_kernel(const DevTables T, const DevIndex I, const uint6
   }
 }
 
+// number of exchange terms per product: every antiparallel bond, and those whose
+// representative is a basis state
+__global__ void count_terms_kernel(const DevTables T, const DevIndex I, const uint8_t *bond_pos,
+                                   int n_bonds, unsigned long long *out) {
+  unsigned long long nf = 0, no = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I.D;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = I.basis[i];
+    for (int b = 0; b < n_bonds; b++) {
+      const int pa = bond_pos[2 * b], pb = bond_pos[2 * b + 1];
+      if ((((s >> pa) ^ (s >> pb)) & 1ULL) == 0) continue;
+      nf++;
+      const RepOut R = find_rep(T, T.rep, T.sym_off, T.sym_list, T.dest, T.phase,
+                                s ^ ((1ULL << pa) | (1ULL << pb)));
+      if (!R.mixed && lookup_index(I, R.rep) >= 0) no++;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nf += __shfl_down_sync(0xFFFFFFFFu, nf, o);
+    no += __shfl_down_sync(0xFFFFFFFFu, no, o);
+  }
+  if ((threadIdx.x & 31) == 0) { atomicAdd(out, nf); atomicAdd(out + 1, no); }
+}
+
 // ------------------------------ vector kernels -------------------------------------
 template <typename V>
 __global__ void dot_kernel(const V *x, const V *y, int64_t n, double *partial) {
@@ -364,6 +388,14 @@ int ed_launch_find_rep(const ed_basis *B, const uint64_t *states, int64_t n, uin
   if (n <= 0) return ED_OK;
   const int grid = grid_for(B, n, 8);
   find_rep_kernel<<<grid, 256, 0, st>>>(B->T, B->I, states, n, rep, sym, stab, index);
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+int ed_launch_count(const ed_basis *B, unsigned long long *d_out, cudaStream_t st) {
+  if (B->D == 0) return ED_OK;
+  count_terms_kernel<<<grid_for(B, B->D, 8), 256, 0, st>>>(B->T, B->I, B->d_bond_pos,
+                                                            B->n_bonds, d_out);
   ED_CK(cudaGetLastError());
   return ED_OK;
 }

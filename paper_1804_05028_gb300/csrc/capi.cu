@@ -489,6 +489,25 @@ extern "C" int ed_dot(ed_basis *B, const void *x, const void *y, int32_t dtype, 
   return reduce_partials(B, B->d_partial, nblk, cplx, st, &out[0], &out[1]);
 }
 
+extern "C" int ed_count_terms(const ed_basis *B, int64_t *n_flip, int64_t *n_offdiag,
+                              void *stream) {
+  if (!B || !n_flip || !n_offdiag) return ed_fail(ED_ERR_INVALID, "null argument");
+  *n_flip = *n_offdiag = 0;
+  if (B->D == 0) return ED_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long *d = nullptr, h[2] = {0, 0};
+  ED_CK(cudaMallocAsync(&d, 16, st));
+  ED_CK(cudaMemsetAsync(d, 0, 16, st));
+  int rc = ed_launch_count(B, d, st);
+  if (rc) return rc;
+  ED_CK(cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, st));
+  ED_CK(cudaFreeAsync(d, st));
+  ED_CK(cudaStreamSynchronize(st));
+  *n_flip = (int64_t)h[0];
+  *n_offdiag = (int64_t)h[1];
+  return ED_OK;
+}
+
 // --------------------------------------------------------------------------------------
 // Lanczos
 // --------------------------------------------------------------------------------------
@@ -595,7 +614,11 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
   L.cplx = o.dtype == ED_C128 || o.dtype == ED_C64;
   L.st = (cudaStream_t)o.stream;
   const size_t bytes = elem_size(o.dtype) * (size_t)B->D;
+  const bool own = o.work == nullptr;
+  if (!own && o.work_bytes < (int64_t)(3 * bytes))
+    return ed_fail(ED_ERR_INVALID, "Lanczos workspace smaller than 3 vectors");
   for (int k = 0; k < 3; k++) {
+    if (!own) { L.v[k] = (char *)o.work + k * bytes; continue; }
     if (cudaMalloc(&L.v[k], bytes) != cudaSuccess) {
       cudaGetLastError();
       for (int q = 0; q < k; q++) cudaFree(L.v[q]);
@@ -638,7 +661,7 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
     if (o.alpha) for (size_t k = 0; k < alpha.size(); k++) o.alpha[k] = alpha[k];
     if (o.beta) for (size_t k = 0; k < beta.size(); k++) o.beta[k] = beta[k];
   }
-  for (int k = 0; k < 3; k++) cudaFree(L.v[k]);
+  if (own) for (int k = 0; k < 3; k++) cudaFree(L.v[k]);
   cudaEventDestroy(L.e0);
   cudaEventDestroy(L.e1);
   res->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

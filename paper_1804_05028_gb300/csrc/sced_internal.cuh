@@ -277,4 +277,5 @@ int ed_launch_scale(const ed_basis *B, void *v, double s, int dtype, cudaStream_
 int ed_launch_axpy(const ed_basis *B, void *y, const void *x, double a, int dtype,
                    cudaStream_t st);
 int ed_launch_start(const ed_basis *B, void *v, uint64_t seed, int dtype, cudaStream_t st);
+int ed_launch_count(const ed_basis *B, unsigned long long *d_out, cudaStream_t st);
 int ed_launch_copy(const ed_basis *B, void *dst, const void *src, int dtype, cudaStream_t st);
