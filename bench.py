@@ -256,13 +256,16 @@ def main():
     # accuracy of the mixed form against fp64 (untimed): full Lanczos runs to convergence
     acc = {}
     if not args.no_accuracy:
-        r64 = B.lanczos(dtype=torch.float64, max_steps=400)
+        psi64 = torch.empty(D, dtype=torch.float64, device="cuda")
+        r64 = B.lanczos(dtype=torch.float64, max_steps=400, psi=psi64)
+        del psi64
         psi32 = torch.empty(D, dtype=torch.float32, device="cuda")
         r32 = B.lanczos(dtype=torch.float32, max_steps=400, psi=psi32)
-        acc = {"E0_f64": r64["E0"], "steps_f64": r64["steps"], "E0_mixed": r32["E0"],
-               "steps_mixed": r32["steps"], "rq_mixed": r32["rq"],
+        acc = {"E0_f64": r64["E0"], "steps_f64": r64["steps"], "rq_f64": r64["rq"],
+               "E0_mixed": r32["E0"], "steps_mixed": r32["steps"], "rq_mixed": r32["rq"],
                "dE0_rel_mixed": abs(r32["E0"] - r64["E0"]) / abs(r64["E0"]),
-               "dE0_rel_mixed_rq": abs(r32["rq"] - r64["E0"]) / abs(r64["E0"])}
+               "dE0_rel_mixed_rq": abs(r32["rq"] - r64["E0"]) / abs(r64["E0"]),
+               "dE0_rel_f64_rq": abs(r64["rq"] - r64["E0"]) / abs(r64["E0"])}
         del psi32
 
     pk, pk_kind = peaks()

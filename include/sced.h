@@ -131,16 +131,21 @@ int ed_basis_info(const ed_basis *basis, ed_basis_info_t *info);
 int ed_basis_export(const ed_basis *basis, uint64_t *states, uint16_t *stab);
 
 /*
- * ed_find_rep -- Alg. 2 (sublattice-coded representative search) plus the Limits
- * lookup, for n arbitrary configurations.  All pointers are DEVICE arrays of length
- * n owned by the caller: states (in), rep (out, Eq. 4 representative), sym (out, the
- * first minimising group element in Sym_Y order; unique up to the stabiliser),
- * stab (out, |Stab(rep)| = number of minimisers), index (out, position of rep in
- * Basis, or -1 when rep is not a basis state: not a surviving representative or a
+ * ed_find_rep -- the representative search alone, plus the Limits lookup, for n arbitrary
+ * configurations.  method 0 is Alg. 2 as printed: MinRep = min_X Rep_X, then every g of
+ * Sym_Y for every minimal Y; method 1 is the two-level search the product uses (Sym_Y is
+ * a coset of the stabiliser of MinRep, searched again by sublattice coding; available for
+ * 2..4 sublattices of <= 11 sites, else ED_ERR_UNSUPPORTED).
+ * All pointers are DEVICE arrays of length n owned by the caller: states (in), rep (out,
+ * Eq. 4 representative), sym (out, method 0: the first minimising element in Sym_Y order,
+ * unique up to the stabiliser; method 1: -1), phase (out, numerator of chi of that
+ * minimiser), stab (out, |Stab(rep)| = number of minimisers), index (out, position of rep
+ * in Basis, or -1 when rep is not a basis state: not a surviving representative or a
  * different n_up).  Asynchronous on stream.  Output pointers may be NULL to skip.
  */
-int ed_find_rep(const ed_basis *basis, const uint64_t *states, int64_t n, uint64_t *rep,
-                int32_t *sym, int32_t *stab, int64_t *index, void *stream);
+int ed_find_rep(const ed_basis *basis, const uint64_t *states, int64_t n, int32_t method,
+                uint64_t *rep, int32_t *sym, int32_t *phase, int32_t *stab, int64_t *index,
+                void *stream);
 
 /*
  * ed_apply_H -- y = H x on the symmetry-adapted basis, matrix-free (Sec. IV,

@@ -108,7 +108,7 @@ def lib():
             L.ed_free_basis.restype = None
             L.ed_basis_info.argtypes = [vp, vp]
             L.ed_basis_export.argtypes = [vp, vp, vp]
-            L.ed_find_rep.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
+            L.ed_find_rep.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp]
             L.ed_apply_H.argtypes = [vp, vp, vp, vp, vp, i32, vp]
             L.ed_apply_H_rows.argtypes = [vp, vp, vp, vp, vp, i32, i64, i64, vp]
             L.ed_apply_H_host.argtypes = [vp, vp, vp, vp, vp, i32, vp]
@@ -212,18 +212,23 @@ class Basis:
             raise ValueError(f"need {self.n_classes} couplings per class")
         return (ctypes.c_double * len(J))(*J), (ctypes.c_double * len(Jz))(*Jz)
 
-    def find_rep(self, states, stream=None):
-        """Alg. 2 on a uint64 CUDA tensor of configurations: (rep, sym, stab, index)."""
+    def find_rep(self, states, method=0, stream=None):
+        """Representative search on a uint64 CUDA tensor of configurations.
+
+        method 0: Alg. 2 as printed; method 1: the two-level search of the product.
+        Returns (rep, sym, phase, stab, index) CUDA tensors.
+        """
         import torch
         n = states.numel()
         dev = states.device
         rep = torch.empty(n, dtype=torch.uint64, device=dev)
         sym = torch.empty(n, dtype=torch.int32, device=dev)
+        ph = torch.empty(n, dtype=torch.int32, device=dev)
         stab = torch.empty(n, dtype=torch.int32, device=dev)
         idx = torch.empty(n, dtype=torch.int64, device=dev)
-        _check(lib().ed_find_rep(self._h, _dev(states, torch.uint64), n, _dev(rep), _dev(sym),
-                                 _dev(stab), _dev(idx), _stream(stream)))
-        return rep, sym, stab, idx
+        _check(lib().ed_find_rep(self._h, _dev(states, torch.uint64), n, int(method), _dev(rep),
+                                 _dev(sym), _dev(ph), _dev(stab), _dev(idx), _stream(stream)))
+        return rep, sym, ph, stab, idx
 
     def apply_H(self, x, y=None, J=None, Jz=None, stream=None):
         """y = H x for CUDA tensors (float64/float32/complex128/complex64)."""

@@ -9,7 +9,7 @@
 // of the push of Alg. 4, exact because H is Hermitian.  Each y_i is written once:
 // no atomics, no inter-block communication, fixed summation order.
 #include "sced_internal.cuh"
-#include <cuda_fp16.h>
+#include <cstdlib>
 
 namespace {
 
@@ -185,13 +185,14 @@ int launch_apply_t(const ApplyParams &P, int grid, cudaStream_t st) {
 }
 
 __global__ void find_rep_kernel(const DevTables T, const DevIndex I, const uint64_t *states,
-                                int64_t n, uint64_t *rep, int32_t *sym, int32_t *stab,
-                                int64_t *index) {
+                                int64_t n, uint64_t *rep, int32_t *sym, int32_t *phase,
+                                int32_t *stab, int64_t *index) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const RepOut R = find_rep(T, T.rep, T.sym_off, T.sym_list, T.dest, T.phase, states[i]);
     if (rep) rep[i] = R.rep;
     if (sym) sym[i] = R.g;
+    if (phase) phase[i] = R.g >= 0 ? T.phase[R.g] : 0;
     if (stab) stab[i] = R.t;
     if (index) index[i] = (R.mixed || I.D == 0) ? -1 : lookup_index(I, R.rep);
   }
@@ -323,6 +324,10 @@ int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const 
                     void *y, int dtype, int64_t r0, int64_t r1, double *partial,
                     cudaStream_t st) {
   if (r1 <= r0) return ED_OK;
+  if (!getenv("SCED_GENERIC_APPLY")) {
+    const int rc = ed_launch_apply_fast(B, J, Jz, x, y, dtype, r0, r1, partial, st);
+    if (rc != ED_ERR_UNSUPPORTED) return rc;
+  }
   ApplyParams P{};
   P.T = B->T;
   P.I = B->I;
@@ -371,6 +376,7 @@ int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const 
   // fixed grid: a whole number of CTAs per SM, grid-stride over rows
   const int grid = grid_for(B, r1 - r0, 8);
   if (partial && grid > B->n_partial / 2) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
+  B->last_apply_grid = grid;
   const bool sg = P.stage_tables != 0;
   switch (dtype) {
     case ED_F64: return sg ? launch_apply_t<double, true>(P, grid, st) : launch_apply_t<double, false>(P, grid, st);
@@ -384,10 +390,11 @@ int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const 
 int ed_apply_grid(const ed_basis *B, int64_t rows) { return grid_for(B, rows, 8); }
 
 int ed_launch_find_rep(const ed_basis *B, const uint64_t *states, int64_t n, uint64_t *rep,
-                       int32_t *sym, int32_t *stab, int64_t *index, cudaStream_t st) {
+                       int32_t *sym, int32_t *phase, int32_t *stab, int64_t *index,
+                       cudaStream_t st) {
   if (n <= 0) return ED_OK;
   const int grid = grid_for(B, n, 8);
-  find_rep_kernel<<<grid, 256, 0, st>>>(B->T, B->I, states, n, rep, sym, stab, index);
+  find_rep_kernel<<<grid, 256, 0, st>>>(B->T, B->I, states, n, rep, sym, phase, stab, index);
   ED_CK(cudaGetLastError());
   return ED_OK;
 }

@@ -1,0 +1,520 @@
+// apply_fast.cu -- the row-pull product y = H x with a two-level representative search
+// and several exchange terms in flight per thread.
+//
+// Two-level search.  In Alg. 2 of arXiv:1804.05028 the candidates of a minimal block Y
+// are Sym_Y(s_Y) = K_R h: the coset of the stabiliser K_R = {k in G_0 : k R = R} of
+// R = MinRep through the first element h.  Hence min over Sym_Y of g s =
+// min over k in K_R of k (h s), and that inner minimum is again a sublattice-coding
+// problem (Eqs. 8-10) for the group K_R acting on blocks 1.., with block 1 in the role
+// of block 0.  Level 1 looks up (Rep_X, h) per block, applies h once; level 2 looks up
+// (Rep^R_X, Sym^R_X) of the images and scans only those candidates.  The candidate
+// scans that dominate a warp's time (the longest Sym list among 32 lanes) shrink from
+// ~20 to ~3 entries on the 6x6 C4v sector.  Every minimiser of the orbit is still
+// visited (all of them lie in the scanned sets), so |Stab| and the character check are
+// exact, as in the single-level search.
+//
+// Per row (one thread): the row's blocks are extracted once; antiparallel bonds come as
+// 32-bit masks (one coupling class per word); each exchange flips one bit in the block of
+// each end.  Tables: Rep_X / first of Sym_X, stabiliser ids, the level-2 tables (when
+// they fit), prefix ranks, bonds and norms in shared memory; SymmetryAction_X in global
+// memory (L1/L2).  The index of the representative: prefix rank, Limits bucket, binary
+// search of the narrow postfixes.  fp32 vectors are summed per row with a compensated
+// (two-float) accumulator, fp64 in fp64.  Each y_i written once; no atomics.
+#include "sced_internal.cuh"
+#include <algorithm>
+
+namespace {
+
+template <typename V> struct Vf;
+template <> struct Vf<double> { using A = double; static constexpr bool cplx = false; };
+template <> struct Vf<float> { using A = float; static constexpr bool cplx = false; };
+template <> struct Vf<double2> { using A = double; static constexpr bool cplx = true; };
+template <> struct Vf<float2> { using A = float; static constexpr bool cplx = true; };
+
+struct TwoParams {
+  int N, n, nsym, denom;
+  int n_classes;
+  int cls_word[ED_MAXCLS + 1];   // words [cls_word[c], cls_word[c+1]) hold class c
+  int nb_cls[ED_MAXCLS];         // real bonds per class (diagonal term)
+  double jh[ED_MAXCLS], jzq[ED_MAXCLS];
+  const uint32_t *e1, *e2, *off2, *top_rank, *limits;
+  const uint16_t *list2, *act;
+  const uint8_t *rid, *dest, *src, *bond_pos;
+  const uint32_t *bond_blk;      // per padded bond: block of each end, bit inside the block
+  const int32_t *phase;
+  const double *sqrt_tab, *rsqrt_tab, *cs;
+  const uint64_t *basis;
+  const uint16_t *stab;
+  const void *postfix;
+  int r_bits, q_bits, post_bits, post_bytes;
+  int L;                         // bits below the top block: (NSUB - 1) n <= 32
+  uint32_t qmask, pmask;
+  int64_t D;
+  const void *x;
+  void *y;
+  int64_t r0, r1;
+  double *partial;
+  uint32_t n_e1, n_e2, n_rid, n_dest, n_bond, n_top, n_sq, n_cs;
+  uint32_t off_bblk, off_e2, off_e1, off_rid, off_dest, off_src, off_phase, off_bond, off_top, off_sq, off_cs,
+      smem_bytes;
+};
+
+struct Sm2 {
+  const uint32_t *e2;    // level-2 tables (shared-memory copy), when staged
+  const uint32_t *bblk;
+  const uint32_t *e1, *top;
+  const uint8_t *rid, *dest, *src, *bond;
+  const int32_t *phase;
+};
+
+struct Rep2 {
+  uint32_t minrep;   // top block of the representative
+  uint32_t low;      // the lower NSUB-1 blocks, block 1 most significant
+  int t, ph, mixed;
+};
+
+template <typename T>
+__device__ __forceinline__ void cp(unsigned char *sm, uint32_t off, const T *g, uint32_t n) {
+  T *d = reinterpret_cast<T *>(sm + off);
+  for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) d[k] = g[k];
+}
+
+// g s restricted to block X: an n-bit value on block dest(g, X) (SymmetryAction_X, Eq. 11)
+__device__ __forceinline__ uint32_t act(const TwoParams &P, int X, uint32_t sub, int g) {
+  return __ldg(P.act + (((uint32_t)X << P.n) | sub) * (uint32_t)P.nsym + (uint32_t)g);
+}
+
+__device__ __forceinline__ void consider(Rep2 &o, uint32_t low, int ph) {
+  if (low < o.low) { o.low = low; o.t = 1; o.ph = ph; o.mixed = 0; }
+  else if (low == o.low) { o.t++; o.mixed |= (ph != o.ph); }
+}
+
+template <int NSUB>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&a)[NSUB], int i) {
+  uint32_t v = a[0];
+#pragma unroll
+  for (int k = 1; k < NSUB; k++) v = (i == k) ? a[k] : v;
+  return v;
+}
+
+// Two-level search (see the file comment) on a configuration given block by block
+// (sub[X] = the n-bit substate of block X).  Candidates share the top block MinRep, so
+// they are compared on the lower NSUB-1 blocks only, packed in 32 bits (block 1 most
+// significant); the result is rep = MinRep << L | low with L = (NSUB-1) n.  Loops run
+// over bitmasks of the minimal blocks so that one copy of each step is emitted.
+template <int NSUB, bool kE2>
+__device__ __forceinline__ Rep2 find_rep_blocks(const Sm2 &S, const TwoParams &P,
+                                                const uint32_t (&sub)[NSUB]) {
+  const int n = P.n;
+  uint32_t e[NSUB];
+  uint32_t minrep = 0xFFFFFFFFu, ymask = 0;
+#pragma unroll
+  for (int X = 0; X < NSUB; X++) {
+    e[X] = S.e1[(X << n) | sub[X]];
+    const uint32_t r = e[X] & 0xFFFu;
+    if (r < minrep) { minrep = r; ymask = 1u << X; }
+    else if (r == minrep) ymask |= 1u << X;
+  }
+  Rep2 o;
+  o.minrep = minrep; o.low = 0xFFFFFFFFu; o.t = 0; o.ph = 0; o.mixed = 0;
+  const int rid = S.rid[minrep];
+  while (ymask) {
+    const int Y = __ffs(ymask) - 1;
+    ymask &= ymask - 1;
+    const int h = (pick<NSUB>(e, Y) >> 12) & 0xFFF;
+    const int phh = S.phase[h];
+    uint32_t tau[NSUB];   // tau[d] = block d of h s
+    tau[0] = minrep;
+#pragma unroll
+    for (int d = 1; d < NSUB; d++) {
+      const int X = S.src[h * NSUB + d];
+      tau[d] = act(P, X, pick<NSUB>(sub, X), h);
+    }
+    if (rid == 0xFF) {   // K_R = {e}: h is the only candidate of this block
+      uint32_t low = 0;
+#pragma unroll
+      for (int d = 1; d < NSUB; d++) low |= tau[d] << ((NSUB - 1 - d) * n);
+      consider(o, low, phh);
+      continue;
+    }
+    const uint32_t rbase = (uint32_t)rid * (NSUB - 1);
+    uint32_t f[NSUB];
+    uint32_t m2 = 0xFFFFFFFFu, dmask = 0;
+#pragma unroll
+    for (int d = 1; d < NSUB; d++) {
+      const uint32_t ei = ((rbase + d - 1) << n) | tau[d];
+      f[d] = kE2 ? S.e2[ei] : __ldg(P.e2 + ei);
+      const uint32_t r2 = f[d] & 0xFFFu;
+      if (r2 < m2) { m2 = r2; dmask = 1u << d; }
+      else if (r2 == m2) dmask |= 1u << d;
+    }
+    f[0] = 0;
+    const uint32_t low2 = m2 << ((NSUB - 2) * n);
+    while (dmask) {
+      const int d2 = __ffs(dmask) - 1;
+      dmask &= dmask - 1;
+      const uint32_t fd = pick<NSUB>(f, d2);
+      const int cnt = fd >> 24;
+      const uint32_t base =
+          cnt > 1 ? __ldg(P.off2 + (((rbase + d2 - 1) << n) | pick<NSUB>(tau, d2))) : 0u;
+      for (int c = 0; c < cnt; c++) {
+        const int k = c == 0 ? (int)((fd >> 12) & 0xFFF) : (int)__ldg(P.list2 + base + c);
+        uint32_t low = low2;
+#pragma unroll
+        for (int d = 1; d < NSUB; d++) {
+          if (d == d2) continue;
+          const int dd = S.dest[k * NSUB + d];
+          low |= act(P, d, tau[d], k) << ((NSUB - 1 - dd) * n);
+        }
+        int ph = phh + S.phase[k];
+        if (ph >= P.denom) ph -= P.denom;
+        consider(o, low, ph);
+      }
+    }
+  }
+  return o;
+}
+
+__device__ __forceinline__ uint32_t ld_post(const TwoParams &P, uint32_t i) {
+  switch (P.post_bytes) {
+    case 1: return __ldg(reinterpret_cast<const uint8_t *>(P.postfix) + i);
+    case 2: return __ldg(reinterpret_cast<const uint16_t *>(P.postfix) + i);
+  }
+  return __ldg(reinterpret_cast<const uint32_t *>(P.postfix) + i);
+}
+
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (v - bb);
+  hi = s;
+}
+
+__device__ __forceinline__ Sm2 stage_two(const TwoParams &P, unsigned char *sm, bool cplx,
+                                         bool e2) {
+  cp(sm, P.off_e1, P.e1, P.n_e1);
+  cp(sm, P.off_rid, P.rid, P.n_rid);
+  cp(sm, P.off_dest, P.dest, P.n_dest);
+  cp(sm, P.off_src, P.src, P.n_dest);
+  cp(sm, P.off_phase, P.phase, (uint32_t)P.nsym);
+  cp(sm, P.off_bond, P.bond_pos, P.n_bond);
+  cp(sm, P.off_bblk, P.bond_blk, P.n_bond / 2);
+  cp(sm, P.off_top, P.top_rank, P.n_top);
+  cp(sm, P.off_sq, P.sqrt_tab, P.n_sq);
+  cp(sm, P.off_sq + 8 * P.n_sq, P.rsqrt_tab, P.n_sq);
+  if (cplx) cp(sm, P.off_cs, P.cs, P.n_cs);
+  if (e2) cp(sm, P.off_e2, P.e2, P.n_e2);
+  __syncthreads();
+  Sm2 S;
+  S.e2 = reinterpret_cast<const uint32_t *>(sm + P.off_e2);
+  S.bblk = reinterpret_cast<const uint32_t *>(sm + P.off_bblk);
+  S.e1 = reinterpret_cast<const uint32_t *>(sm + P.off_e1);
+  S.rid = sm + P.off_rid;
+  S.dest = sm + P.off_dest;
+  S.src = sm + P.off_src;
+  S.phase = reinterpret_cast<const int32_t *>(sm + P.off_phase);
+  S.bond = sm + P.off_bond;
+  S.top = reinterpret_cast<const uint32_t *>(sm + P.off_top);
+  return S;
+}
+
+// Index of the representative MinRep << L | low in Basis: prefix rank (shared memory),
+// Limits bucket, binary search of the postfixes in the bucket (Sec. IV); -1 when absent.
+// The fast path has N - r_bits <= 32, so the bucket key's raw bits and the postfix are
+// taken from the low 32 bits of the state.
+__device__ __forceinline__ int64_t lookup_two(const Sm2 &S, const TwoParams &P, uint32_t minrep,
+                                              uint32_t low) {
+  const uint64_t r = ((uint64_t)minrep << P.L) | low;
+  const uint32_t rk = S.top[(uint32_t)(r >> (P.N - P.r_bits))];
+  if (rk == ED_NO_RANK) return -1;
+  const uint32_t key = (rk << P.q_bits) | ((uint32_t)(r >> P.post_bits) & P.qmask);
+  uint32_t lo = __ldg(P.limits + key), hi = __ldg(P.limits + key + 1);
+  const uint32_t tg = (uint32_t)r & P.pmask;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const uint32_t pv = ld_post(P, mid);
+    if (pv < tg) lo = mid + 1;
+    else if (pv > tg) hi = mid;
+    else return mid;
+  }
+  return -1;
+}
+
+template <typename V, int NSUB, bool kE2>
+__global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : 2) apply_two_kernel(const TwoParams P) {
+  using A = typename Vf<V>::A;
+  constexpr bool kC = Vf<V>::cplx;
+  constexpr bool kF32 = sizeof(A) == 4;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const Sm2 S = stage_two(P, sm, kC, kE2);
+  const double *sqd = reinterpret_cast<const double *>(sm + P.off_sq);
+  const double *rsd = sqd + P.n_sq;
+  const double *csd = reinterpret_cast<const double *>(sm + P.off_cs);
+  const V *x = reinterpret_cast<const V *>(P.x);
+  V *y = reinterpret_cast<V *>(P.y);
+  const int N = P.N, n = P.n;
+  const uint32_t bmask = (1u << n) - 1u;
+
+  double dot_re = 0.0, dot_im = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = P.r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.r1; i += stride) {
+    const uint64_t s = __ldg(P.basis + i);
+    const int ti = __ldg(P.stab + i);
+    uint32_t sub[NSUB];
+#pragma unroll
+    for (int X = 0; X < NSUB; X++) sub[X] = (uint32_t)(s >> (N - (X + 1) * n)) & bmask;
+    double row_re = 0.0, row_im = 0.0, diag = 0.0;
+    for (int c = 0; c < P.n_classes; c++) {
+      A acc_re = 0, acc_im = 0;
+      float lo_re = 0.f;   // compensation (fp32 real vectors)
+      int nanti = 0;
+      for (int wd = P.cls_word[c]; wd < P.cls_word[c + 1]; wd++) {
+        const uint8_t *bp = S.bond + wd * 64;
+        uint32_t m = 0;
+#pragma unroll 8
+        for (int k = 0; k < 32; k++)
+          m |= (uint32_t)(((s >> bp[2 * k]) ^ (s >> bp[2 * k + 1])) & 1ULL) << k;
+        nanti += __popc(m);
+        while (m) {
+          const int k = __ffs(m) - 1;
+          m &= m - 1;
+          // the exchanged configuration, block by block: one bit flips in the block of
+          // each end of the bond
+          const uint32_t bi = S.bblk[wd * 32 + k];
+          const int xa = bi & 15, xb = (bi >> 4) & 15;
+          const uint32_t fa = 1u << ((bi >> 8) & 255), fb = 1u << (bi >> 16);
+          uint32_t s2[NSUB];
+#pragma unroll
+          for (int X = 0; X < NSUB; X++) s2[X] = sub[X] ^ (X == xa ? fa : 0u) ^ (X == xb ? fb : 0u);
+          const Rep2 R = find_rep_blocks<NSUB, kE2>(S, P, s2);
+          if (R.mixed) continue;
+          const int64_t j = lookup_two(S, P, R.minrep, R.low);
+          if (j < 0) continue;
+          const V xj = x[j];
+          const int t = R.t, ph = R.ph;
+          if constexpr (!kC) {
+            if constexpr (kF32) {
+              if (t == 1) {
+                two_sum(acc_re, lo_re, ph == 0 ? xj : -xj);
+              } else {
+                const double w = sqd[t];
+                const float wh = (float)w, wl = (float)(w - (double)wh);
+                const float p = wh * xj;
+                const float pe = fmaf(wh, xj, -p) + wl * xj;
+                two_sum(acc_re, lo_re, ph == 0 ? p : -p);
+                lo_re += ph == 0 ? pe : -pe;
+              }
+            } else {
+              const double v = (t == 1) ? (double)xj : sqd[t] * (double)xj;
+              acc_re += ph == 0 ? v : -v;
+            }
+          } else {
+            const A wgt = (A)sqd[t];
+            const A cr = (A)csd[2 * ph] * wgt, ci = (A)csd[2 * ph + 1] * wgt;
+            acc_re += cr * xj.x - ci * xj.y;
+            acc_im += cr * xj.y + ci * xj.x;
+          }
+        }
+      }
+      diag += P.jzq[c] * (double)(P.nb_cls[c] - 2 * nanti);
+      row_re += P.jh[c] * ((double)acc_re + (double)lo_re);
+      if (kC) row_im += P.jh[c] * (double)acc_im;
+    }
+    const double rs = rsd[ti];
+    if constexpr (!kC) {
+      const double xi = (double)x[i];
+      const A yi = (A)(diag * xi + row_re * rs);
+      y[i - P.r0] = yi;
+      if (P.partial) dot_re += xi * (double)yi;
+    } else {
+      const V xv = x[i];
+      V yv;
+      yv.x = (A)(diag * (double)xv.x + row_re * rs);
+      yv.y = (A)(diag * (double)xv.y + row_im * rs);
+      y[i - P.r0] = yv;
+      if (P.partial) {
+        dot_re += (double)xv.x * yv.x + (double)xv.y * yv.y;
+        dot_im += (double)xv.x * yv.y - (double)xv.y * yv.x;
+      }
+    }
+  }
+  if (P.partial) {
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int part = 0; part < (kC ? 2 : 1); part++) {
+      double d = part ? dot_im : dot_re;
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xFFFFFFFFu, d, o);
+      __syncthreads();
+      if (lane == 0) red[wid] = d;
+      __syncthreads();
+      if (wid == 0) {
+        d = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xFFFFFFFFu, d, o);
+        if (lane == 0) P.partial[part * gridDim.x + blockIdx.x] = d;
+      }
+    }
+  }
+}
+
+// test hook: the two-level search alone
+template <int NSUB, bool kE2>
+__global__ void find_rep_two_kernel(const TwoParams P, const DevIndex I, const uint64_t *states,
+                                    int64_t n, uint64_t *rep, int32_t *phase, int32_t *stab,
+                                    int64_t *index) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const Sm2 S = stage_two(P, sm, false, kE2);
+  const uint32_t bmask = (1u << P.n) - 1u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t sub[NSUB];
+#pragma unroll
+    for (int X = 0; X < NSUB; X++) sub[X] = (uint32_t)(states[i] >> (P.N - (X + 1) * P.n)) & bmask;
+    const Rep2 R = find_rep_blocks<NSUB, kE2>(S, P, sub);
+    const uint64_t r = ((uint64_t)R.minrep << P.L) | R.low;
+    if (rep) rep[i] = r;
+    if (phase) phase[i] = R.ph;
+    if (stab) stab[i] = R.t;
+    if (index) index[i] = (R.mixed || I.D == 0) ? -1 : lookup_index(I, r);
+  }
+}
+
+size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Parameters and shared-memory layout; e2 = stage the level-2 tables in shared memory.
+int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, TwoParams &P) {
+  if (!B->two_level || B->nsub < 2 || B->nsub > 4 || B->I.r_bits > 12 || B->D == 0 ||
+      (B->nsub - 1) * B->n > 32 || B->N - B->I.r_bits > 32)
+    return ED_ERR_UNSUPPORTED;
+  P = TwoParams{};
+  P.N = B->N; P.n = B->n; P.nsym = B->nsym; P.denom = B->denom;
+  P.n_classes = B->n_classes;
+  for (int c = 0; c <= B->n_classes; c++) P.cls_word[c] = B->cls_word[c];
+  for (int c = 0; c < B->n_classes; c++) {
+    P.nb_cls[c] = B->cls_off[c + 1] - B->cls_off[c];
+    P.jh[c] = J ? 0.5 * J[c] : 0.0;
+    P.jzq[c] = J ? 0.25 * J[c] * Jz[c] : 0.0;
+  }
+  P.e1 = B->d_e1; P.e2 = B->d_e2; P.off2 = B->d_off2; P.list2 = B->d_list2; P.rid = B->d_rid;
+  P.act = (const uint16_t *)B->d_action;
+  P.dest = B->d_dest; P.src = B->d_src; P.phase = B->d_phase;
+  P.bond_pos = B->d_bond_pad; P.top_rank = B->d_top_rank; P.limits = B->d_limits;
+  P.sqrt_tab = B->d_sqrt; P.rsqrt_tab = B->d_rsqrt; P.cs = B->d_cs;
+  P.basis = B->d_basis; P.stab = B->d_stab; P.postfix = B->d_postfix;
+  P.r_bits = B->I.r_bits; P.q_bits = B->I.q_bits; P.post_bits = B->I.post_bits;
+  P.post_bytes = B->I.post_bytes; P.D = B->D;
+  P.L = (B->nsub - 1) * B->n;
+  P.qmask = P.q_bits >= 32 ? 0xFFFFFFFFu : ((1u << P.q_bits) - 1u);
+  P.pmask = P.post_bits >= 32 ? 0xFFFFFFFFu : ((1u << P.post_bits) - 1u);
+  P.bond_blk = B->d_bond_blk;
+  const uint32_t nn = 1u << B->n;
+  P.n_e1 = (uint32_t)B->nsub * nn;
+  P.n_rid = nn;
+  P.n_dest = (uint32_t)B->nsym * B->nsub;
+  P.n_bond = (uint32_t)B->cls_word[B->n_classes] * 64;
+  P.n_top = 1u << B->I.r_bits;
+  P.n_sq = (uint32_t)B->nsym + 1;
+  P.n_cs = 2u * B->denom;
+  P.n_e2 = e2 ? (uint32_t)B->n_rid * (B->nsub - 1) * nn : 0u;
+  size_t off = 0;
+  auto put = [&](uint32_t &o, size_t bytes) { o = (uint32_t)off; off += a16(bytes); };
+  put(P.off_sq, 16 * (size_t)P.n_sq);
+  put(P.off_cs, 8 * (size_t)P.n_cs);
+  put(P.off_e1, 4 * (size_t)P.n_e1);
+  put(P.off_top, 4 * (size_t)P.n_top);
+  put(P.off_phase, 4 * (size_t)P.nsym);
+  put(P.off_e2, 4 * (size_t)P.n_e2);
+  put(P.off_bblk, 2 * (size_t)P.n_bond);
+  put(P.off_rid, P.n_rid);
+  put(P.off_dest, P.n_dest);
+  put(P.off_src, P.n_dest);
+  put(P.off_bond, P.n_bond);
+  P.smem_bytes = (uint32_t)off;
+  if (off > (e2 ? 180 : 100) * 1024) return ED_ERR_UNSUPPORTED;
+  return ED_OK;
+}
+
+// e2 staged: one 1024-thread CTA per SM (the tables take most of shared memory);
+// otherwise two 512-thread CTAs per SM.  Both give 32 warps per SM at 64 registers.
+template <typename V, int NSUB>
+int launch_t(const TwoParams &P, bool e2, int grid, cudaStream_t st) {
+  if (e2) {
+    auto k = apply_two_kernel<V, NSUB, true>;
+    ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
+    k<<<grid, 1024, P.smem_bytes, st>>>(P);
+  } else {
+    auto k = apply_two_kernel<V, NSUB, false>;
+    ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
+    k<<<grid, 512, P.smem_bytes, st>>>(P);
+  }
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+template <typename V>
+int launch_v(const TwoParams &P, bool e2, int nsub, int grid, cudaStream_t st) {
+  switch (nsub) {
+    case 2: return launch_t<V, 2>(P, e2, grid, st);
+    case 3: return launch_t<V, 3>(P, e2, grid, st);
+    case 4: return launch_t<V, 4>(P, e2, grid, st);
+  }
+  return ED_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+// The two-level path applies when its tables exist (2..4 sublattices of <= 11 sites,
+// |G| <= 4096); returns ED_ERR_UNSUPPORTED otherwise (the caller uses the generic kernel).
+int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
+                         void *y, int dtype, int64_t r0, int64_t r1, double *partial,
+                         cudaStream_t st) {
+  TwoParams P;
+  bool e2 = true;
+  int rc = make_params(B, J, Jz, e2, P);
+  if (rc == ED_ERR_UNSUPPORTED) { e2 = false; rc = make_params(B, J, Jz, false, P); }
+  if (rc) return rc;
+  P.x = x; P.y = y; P.r0 = r0; P.r1 = r1; P.partial = partial;
+  const int bs = e2 ? 1024 : 512;
+  int grid = B->sm_count * (e2 ? 1 : 2);
+  const int64_t need = (r1 - r0 + bs - 1) / bs;
+  if (need < grid) grid = (int)need;
+  if (grid < 1) grid = 1;
+  if (partial && grid > B->n_partial / 2) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
+  B->last_apply_grid = grid;
+  switch (dtype) {
+    case ED_F64: return launch_v<double>(P, e2, B->nsub, grid, st);
+    case ED_F32: return launch_v<float>(P, e2, B->nsub, grid, st);
+    case ED_C128: return launch_v<double2>(P, e2, B->nsub, grid, st);
+    case ED_C64: return launch_v<float2>(P, e2, B->nsub, grid, st);
+  }
+  return ed_fail(ED_ERR_INVALID, "unknown dtype");
+}
+
+int ed_launch_find_rep_two(const ed_basis *B, const uint64_t *states, int64_t n, uint64_t *rep,
+                           int32_t *phase, int32_t *stab, int64_t *index, cudaStream_t st) {
+  TwoParams P;
+  bool e2 = true;
+  int rc = make_params(B, nullptr, nullptr, e2, P);
+  if (rc == ED_ERR_UNSUPPORTED) { e2 = false; rc = make_params(B, nullptr, nullptr, false, P); }
+  if (rc == ED_ERR_UNSUPPORTED) return ed_fail(rc, "two-level search not available for this sector");
+  if (rc) return rc;
+  if (n <= 0) return ED_OK;
+  int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)B->sm_count * 4);
+  switch (B->nsub * 2 + (e2 ? 1 : 0)) {
+#define L2CASE(K, C)                                                                           \
+  case K * 2 + C: {                                                                            \
+    auto k = find_rep_two_kernel<K, C>;                                                        \
+    ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes)); \
+    k<<<grid, 256, P.smem_bytes, st>>>(P, B->I, states, n, rep, phase, stab, index);           \
+    break;                                                                                     \
+  }
+    L2CASE(2, 0)
+    L2CASE(3, 0)
+    L2CASE(4, 0)
+    L2CASE(2, 1)
+    L2CASE(3, 1)
+    L2CASE(4, 1)
+#undef L2CASE
+  }
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}

@@ -365,7 +365,7 @@ int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target) {
   if (D == 0) return ED_OK;
 
   // ---- prefix index ----
-  const int r_bits = std::min(N, 16);
+  const int r_bits = std::min(N, 12);
   const uint64_t ntop = 1ULL << r_bits;
   uint32_t *d_flags = nullptr, *d_rank_top = nullptr;
   uint64_t *d_scan = nullptr;
@@ -407,16 +407,20 @@ int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target) {
   ED_CK(cudaGetLastError());
   unsigned long long mb = 0;
   ED_CK(cudaMemcpyAsync(&mb, d_max, 8, cudaMemcpyDeviceToHost, st));
-  const int post_bytes = post_bits <= 16 ? 2 : post_bits <= 32 ? 4 : 8;
+  const int post_bytes = post_bits <= 8 ? 1 : post_bits <= 16 ? 2 : post_bits <= 32 ? 4 : 8;
   const uint64_t pmask = post_bits >= 64 ? ~0ULL : ((1ULL << post_bits) - 1ULL);
   if (post_bytes == 8) {
     B->d_postfix = B->d_basis;   // full states are the postfixes
   } else {
-    if (cudaMalloc(&B->d_postfix, (size_t)D * post_bytes) != cudaSuccess) {
+    // 32 bytes of zero padding: the bucket reader loads whole 16-byte chunks
+    if (cudaMalloc(&B->d_postfix, (size_t)D * post_bytes + 32) != cudaSuccess) {
       cudaGetLastError();
       return ed_fail(ED_ERR_OOM, "cannot allocate postfixes");
     }
-    if (post_bytes == 2)
+    ED_CK(cudaMemsetAsync((char *)B->d_postfix + (size_t)D * post_bytes, 0, 32, st));
+    if (post_bytes == 1)
+      make_postfix<uint8_t><<<g1, 256, 0, st>>>(B->d_basis, B->D, pmask, (uint8_t *)B->d_postfix);
+    else if (post_bytes == 2)
       make_postfix<uint16_t><<<g1, 256, 0, st>>>(B->d_basis, B->D, pmask, (uint16_t *)B->d_postfix);
     else
       make_postfix<uint32_t><<<g1, 256, 0, st>>>(B->d_basis, B->D, pmask, (uint32_t *)B->d_postfix);

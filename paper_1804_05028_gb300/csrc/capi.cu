@@ -23,7 +23,6 @@ int ed_cuda_fail(cudaError_t e, const char *what) {
   return ED_ERR_CUDA;
 }
 
-int ed_apply_grid(const ed_basis *B, int64_t rows);
 
 extern "C" const char *ed_last_error(void) { return g_err.c_str(); }
 extern "C" const char *ed_version(void) { return "sced 0.1 (sm_103a)"; }
@@ -154,6 +153,27 @@ int validate(ed_basis *B, const ed_lattice *L, const ed_group *G, const ed_irrep
       }
   }
   B->cls_off[B->n_classes] = (int)B->bond_pos.size() / 2;
+  // the same bonds padded per class to whole words of 32 with inert bonds (0, 0)
+  B->cls_word.assign(B->n_classes + 1, 0);
+  B->bond_pad.clear();
+  for (int c = 0; c < B->n_classes; c++) {
+    B->cls_word[c] = (int)B->bond_pad.size() / 64;
+    for (int b = B->cls_off[c]; b < B->cls_off[c + 1]; b++) {
+      B->bond_pad.push_back(B->bond_pos[2 * b]);
+      B->bond_pad.push_back(B->bond_pos[2 * b + 1]);
+    }
+    while (B->bond_pad.size() % 64) B->bond_pad.push_back(0);
+  }
+  B->cls_word[B->n_classes] = (int)B->bond_pad.size() / 64;
+  // the same bonds as (block, bit inside the block) pairs, bit counted from the block's LSB
+  B->bond_blk.assign(B->bond_pad.size() / 2, 0);
+  for (size_t b = 0; b < B->bond_blk.size(); b++) {
+    const int pa = B->bond_pad[2 * b], pb = B->bond_pad[2 * b + 1];
+    if (pa == pb) continue;   // inert padding
+    const int la = N - 1 - pa, lb = N - 1 - pb;
+    B->bond_blk[b] = (uint32_t)(la / n) | ((uint32_t)(lb / n) << 4) |
+                     ((uint32_t)(n - 1 - la % n) << 8) | ((uint32_t)(n - 1 - lb % n) << 16);
+  }
   return ED_OK;
 }
 
@@ -202,6 +222,54 @@ int build_tables(ed_basis *B, cudaStream_t st) {
     symoff[(size_t)X * (nn + 1) + nn] = (uint32_t)symlist.size();
   }
   if (symlist.size() >= 0xFFFFFFFFull) return ed_fail(ED_ERR_UNSUPPORTED, "Sym lists too long");
+  // Two-level search tables.  Sym_Y(s_Y) is the coset K_R h of the stabiliser
+  // K_R = {k in G_0 : k R = R} of R = Rep_Y(s_Y), h its first element; so
+  // min over Sym_Y of g s = min over k in K_R of k (h s), and the inner minimum is again
+  // a sublattice-coding problem, for the group K_R on blocks 1.. (Eqs. 8-10 with
+  // block 1 in the role of block 0).  Level 1 keeps only (Rep_X, first element of
+  // Sym_X); level 2 holds, for every R with a nontrivial K_R, Rep^R_X and Sym^R_X.
+  // Entries: level 1 rep | h << 12;  level 2 rep | first << 12 | count << 24, and the
+  // offset of the full list; a block that no element of K_R carries onto block 1 gets the
+  // sentinel rep 0xFFF (above every n-bit value).  Needs n <= 11, |G| <= 4096, lists <=
+  // 255 entries and fewer than 255 such R.
+  std::vector<uint32_t> e1, e2, off2;
+  std::vector<uint16_t> list2;
+  std::vector<uint8_t> rid, src((size_t)ns * nsub, 0);
+  for (int g = 0; g < ns; g++)
+    for (int X = 0; X < nsub; X++) src[(size_t)g * nsub + dest[(size_t)g * nsub + X]] = (uint8_t)X;
+  bool two = need_action && nsub <= 4 && n <= 11 && ns <= 4096;
+  int nrid = 0;
+  if (two) {
+    e1.resize((size_t)nsub * nn);
+    for (int X = 0; X < nsub; X++)
+      for (size_t sub = 0; sub < nn; sub++)
+        e1[(size_t)X * nn + sub] = rep[(size_t)X * nn + sub] |
+                                   ((uint32_t)symlist[symoff[(size_t)X * (nn + 1) + sub]] << 12);
+    rid.assign(nn, 0xFF);
+    std::vector<int> G0;
+    for (int g = 0; g < ns; g++) if (dest[(size_t)g * nsub] == 0) G0.push_back(g);
+    for (size_t R = 0; R < nn && two; R++) {
+      if (rep[R] != R) continue;   // only Rep_0 fixed points can be MinRep
+      std::vector<int> K;
+      for (int g : G0) if (act16[((size_t)0 * nn + R) * ns + g] == R) K.push_back(g);
+      if (K.size() <= 1) continue;
+      if (nrid >= 254) { two = false; break; }
+      rid[R] = (uint8_t)nrid++;
+      for (int d = 1; d < nsub && two; d++)
+        for (size_t sub = 0; sub < nn; sub++) {
+          uint32_t best = 0xFFFFFFFFu;
+          for (int k : K)
+            if (dest[(size_t)k * nsub + d] == 1) best = std::min<uint32_t>(best, act16[((size_t)d * nn + sub) * ns + k]);
+          const uint32_t o = (uint32_t)list2.size();
+          for (int k : K)
+            if (dest[(size_t)k * nsub + d] == 1 && act16[((size_t)d * nn + sub) * ns + k] == best) list2.push_back((uint16_t)k);
+          const uint32_t cnt = (uint32_t)list2.size() - o;
+          if (cnt > 255) { two = false; break; }
+          e2.push_back(cnt ? (best | ((uint32_t)list2[o] << 12) | (cnt << 24)) : 0xFFFu);
+          off2.push_back(o);
+        }
+    }
+  }
   auto up = [&](void **dst, const void *src, size_t bytes) -> int {
     if (bytes == 0) { *dst = nullptr; return ED_OK; }
     if (cudaMalloc(dst, bytes) != cudaSuccess) { cudaGetLastError(); return ed_fail(ED_ERR_OOM, "cannot allocate lookup tables"); }
@@ -212,9 +280,22 @@ int build_tables(ed_basis *B, cudaStream_t st) {
   int rc;
   if ((rc = up((void **)&B->d_rep, rep.data(), rep.size() * 4))) return rc;
   if ((rc = up((void **)&B->d_sym_off, symoff.data(), symoff.size() * 4))) return rc;
-  if ((rc = up((void **)&B->d_sym_list, symlist.data(), std::max<size_t>(symlist.size(), 1) * 2))) return rc;
+  if (symlist.empty()) symlist.push_back(0);
+  if ((rc = up((void **)&B->d_sym_list, symlist.data(), symlist.size() * 2))) return rc;
   if ((rc = up((void **)&B->d_dest, dest.data(), dest.size()))) return rc;
   if ((rc = up((void **)&B->d_phase, B->phase.data(), B->phase.size() * 4))) return rc;
+  if ((rc = up((void **)&B->d_src, src.data(), src.size()))) return rc;
+  if (two) {
+    if (e2.empty()) { e2.push_back(0xFFFu); off2.push_back(0); }
+    if (list2.empty()) list2.push_back(0);
+    if ((rc = up((void **)&B->d_e1, e1.data(), e1.size() * 4))) return rc;
+    if ((rc = up((void **)&B->d_rid, rid.data(), rid.size()))) return rc;
+    if ((rc = up((void **)&B->d_e2, e2.data(), e2.size() * 4))) return rc;
+    if ((rc = up((void **)&B->d_off2, off2.data(), off2.size() * 4))) return rc;
+    if ((rc = up((void **)&B->d_list2, list2.data(), list2.size() * 2))) return rc;
+    B->two_level = true;
+    B->n_rid = nrid;
+  }
   if (need_action) {
     if (u16) { if ((rc = up(&B->d_action, act16.data(), act16.size() * 2))) return rc; }
     else { if ((rc = up(&B->d_action, act32.data(), act32.size() * 4))) return rc; }
@@ -237,12 +318,16 @@ int build_tables(ed_basis *B, cudaStream_t st) {
   if ((rc = up((void **)&B->d_rsqrt, rs.data(), rs.size() * 8))) return rc;
   if ((rc = up((void **)&B->d_cs, cs.data(), cs.size() * 8))) return rc;
   if ((rc = up((void **)&B->d_bond_pos, B->bond_pos.data(), B->bond_pos.size()))) return rc;
+  if ((rc = up((void **)&B->d_bond_pad, B->bond_pad.data(), B->bond_pad.size()))) return rc;
+  if ((rc = up((void **)&B->d_bond_blk, B->bond_blk.data(), B->bond_blk.size() * 4))) return rc;
   ED_CK(cudaStreamSynchronize(st));
   return ED_OK;
 }
 
 void free_all(ed_basis *B) {
   void *ptrs[] = {B->d_rep, B->d_sym_off, B->d_sym_list, B->d_action, B->d_dest, B->d_phase,
+                  B->d_src, B->d_e1, B->d_rid, B->d_e2, B->d_off2, B->d_list2, B->d_bond_pad,
+                  B->d_bond_blk,
                   B->d_basis, B->d_stab, B->d_top_rank, B->d_limits,
                   B->d_postfix == B->d_basis ? nullptr : B->d_postfix,
                   B->d_sqrt, B->d_rsqrt, B->d_cs, B->d_bond_pos, B->d_partial,
@@ -423,10 +508,15 @@ extern "C" int ed_basis_export(const ed_basis *B, uint64_t *states, uint16_t *st
   return ED_OK;
 }
 
-extern "C" int ed_find_rep(const ed_basis *B, const uint64_t *states, int64_t n, uint64_t *rep,
-                           int32_t *sym, int32_t *stab, int64_t *index, void *stream) {
+extern "C" int ed_find_rep(const ed_basis *B, const uint64_t *states, int64_t n, int32_t method,
+                           uint64_t *rep, int32_t *sym, int32_t *phase, int32_t *stab,
+                           int64_t *index, void *stream) {
   if (!B || (n > 0 && !states)) return ed_fail(ED_ERR_INVALID, "null argument");
-  return ed_launch_find_rep(B, states, n, rep, sym, stab, index, (cudaStream_t)stream);
+  if (method == 0)
+    return ed_launch_find_rep(B, states, n, rep, sym, phase, stab, index, (cudaStream_t)stream);
+  if (method != 1) return ed_fail(ED_ERR_INVALID, "method must be 0 or 1");
+  if (sym && n > 0) ED_CK(cudaMemsetAsync(sym, 0xFF, (size_t)n * 4, (cudaStream_t)stream));
+  return ed_launch_find_rep_two(B, states, n, rep, phase, stab, index, (cudaStream_t)stream);
 }
 
 extern "C" int ed_apply_H_rows(const ed_basis *B, const double *J, const double *Jz,
@@ -529,7 +619,6 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
                  std::vector<double> &alpha, std::vector<double> &beta, double *E0, int *steps,
                  int *converged, const std::vector<double> *coef, void *psi) {
   ed_basis *B = L.B;
-  const int nblk_apply = ed_apply_grid(B, B->D);
   const int nblk = B->n_partial / 2;
   void *vprev = L.v[0], *v = L.v[1], *w = L.v[2];
   int rc;
@@ -559,7 +648,7 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
     if (replay) {
       a = alpha[j];
     } else {
-      if ((rc = reduce_partials(B, B->d_partial, nblk_apply, L.cplx, L.st, &a, nullptr))) return rc;
+      if ((rc = reduce_partials(B, B->d_partial, B->last_apply_grid, L.cplx, L.st, &a, nullptr))) return rc;
     }
     float ms = 0;
     ED_CK(cudaEventSynchronize(L.e1));
@@ -649,7 +738,7 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
       if (!rc) rc = ed_launch_scale(B, o.psi, 1.0 / std::sqrt(nn), o.dtype, L.st);
       if (!rc) rc = ed_launch_apply(B, J, Jz, o.psi, L.v[0], o.dtype, 0, B->D, B->d_partial, L.st);
       double rq = 0;
-      if (!rc) rc = reduce_partials(B, B->d_partial, ed_apply_grid(B, B->D), L.cplx, L.st, &rq, nullptr);
+      if (!rc) rc = reduce_partials(B, B->d_partial, B->last_apply_grid, L.cplx, L.st, &rq, nullptr);
       res->rq = rq;
     }
   }

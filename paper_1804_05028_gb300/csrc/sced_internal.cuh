@@ -40,7 +40,7 @@ struct DevTables {
 //   postfix[i] = basis[i] & (2^post_bits - 1): what the in-bucket binary search compares
 struct DevIndex {
   int N, r_bits, q_bits, post_bits;
-  int post_bytes;  // 2, 4 or 8
+  int post_bytes;  // 1, 2, 4 or 8
   int64_t D;
   const uint64_t *basis;
   const uint16_t *stab;
@@ -192,6 +192,9 @@ __device__ __forceinline__ int64_t lookup_index(const DevIndex &I, uint64_t s) {
   const uint32_t lo = __ldg(I.limits + key), hi = __ldg(I.limits + key + 1);
   const uint64_t pmask = (I.post_bits >= 64) ? ~0ULL : ((1ULL << I.post_bits) - 1ULL);
   const uint64_t p = s & pmask;
+  if (I.post_bytes == 1)
+    return bucket_search<uint8_t>(reinterpret_cast<const uint8_t *>(I.postfix), lo, hi,
+                                  (uint8_t)p);
   if (I.post_bytes == 2)
     return bucket_search<uint16_t>(reinterpret_cast<const uint16_t *>(I.postfix), lo, hi,
                                    (uint16_t)p);
@@ -223,12 +226,24 @@ struct ed_basis {
   std::vector<int32_t> perm, phase;
   std::vector<uint8_t> bond_pos;       // [n_bonds][2] bit positions (class-sorted)
   std::vector<int32_t> cls_off;        // [n_classes+1] bond ranges per class
+  std::vector<uint8_t> bond_pad;       // bonds padded per class to words of 32 (inert (0,0))
+  std::vector<int32_t> cls_word;       // [n_classes+1] word ranges per class
+  std::vector<uint32_t> bond_blk;      // padded bonds: block | block << 4 | bit << 8 | bit << 16
   // tables
   DevTables T{};
   uint32_t *d_rep = nullptr, *d_sym_off = nullptr;
   uint16_t *d_sym_list = nullptr;
   void *d_action = nullptr;
   uint8_t *d_dest = nullptr;
+  uint8_t *d_src = nullptr;            // [nsym][nsub]: block carried onto block d
+  // two-level search (level 1: Rep_X | first of Sym_X << 12; level 2 per stabiliser K_R)
+  bool two_level = false;
+  int n_rid = 0;
+  uint32_t *d_e1 = nullptr, *d_e2 = nullptr, *d_off2 = nullptr;
+  uint8_t *d_rid = nullptr;
+  uint16_t *d_list2 = nullptr;
+  uint8_t *d_bond_pad = nullptr;
+  uint32_t *d_bond_blk = nullptr;
   int32_t *d_phase = nullptr;
   size_t sym_list_len = 0;
   size_t table_bytes = 0;
@@ -248,6 +263,7 @@ struct ed_basis {
   // scratch
   double *d_partial = nullptr;
   int n_partial = 0;
+  mutable int last_apply_grid = 0;     // grid of the last product (number of dot partials)
   double *h_partial = nullptr;   // pinned
   void *d_stage_x = nullptr, *d_stage_y = nullptr;
   size_t stage_bytes = 0;
@@ -268,7 +284,10 @@ int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target);
 int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const void *x, void *y,
                     int dtype, int64_t r0, int64_t r1, double *partial, cudaStream_t st);
 int ed_launch_find_rep(const ed_basis *B, const uint64_t *states, int64_t n, uint64_t *rep,
-                       int32_t *sym, int32_t *stab, int64_t *index, cudaStream_t st);
+                       int32_t *sym, int32_t *phase, int32_t *stab, int64_t *index,
+                       cudaStream_t st);
+int ed_launch_find_rep_two(const ed_basis *B, const uint64_t *states, int64_t n, uint64_t *rep,
+                           int32_t *phase, int32_t *stab, int64_t *index, cudaStream_t st);
 int ed_launch_dot(const ed_basis *B, const void *x, const void *y, int dtype, double *partial,
                   int nblk, cudaStream_t st);
 int ed_launch_axpy_norm(const ed_basis *B, void *w, const void *v, const void *vprev, double a,
@@ -277,5 +296,8 @@ int ed_launch_scale(const ed_basis *B, void *v, double s, int dtype, cudaStream_
 int ed_launch_axpy(const ed_basis *B, void *y, const void *x, double a, int dtype,
                    cudaStream_t st);
 int ed_launch_start(const ed_basis *B, void *v, uint64_t seed, int dtype, cudaStream_t st);
+int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
+                         void *y, int dtype, int64_t r0, int64_t r1, double *partial,
+                         cudaStream_t st);
 int ed_launch_count(const ed_basis *B, unsigned long long *d_out, cudaStream_t st);
 int ed_launch_copy(const ed_basis *B, void *dst, const void *src, int dtype, cudaStream_t st);

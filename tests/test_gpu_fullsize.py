@@ -54,13 +54,16 @@ def _check_sector(p, n_basis_samples, n_config_samples, n_rows):
     assert np.array_equal(stab, t[pick].astype(np.int32))
     # arbitrary configurations through find_rep
     cfg = _random_configs(p.n_sites, p.n_up, n_config_samples, 1805)
-    rt, gt, st, it = B.find_rep(torch.from_numpy(cfg.view(np.int64)).cuda().view(torch.uint64))
-    rt = rt.cpu().view(torch.int64).numpy().view(np.uint64)
-    st, it = st.cpu().numpy(), it.cpu().numpy()
     orep, og, ostab, okept = oracle.representatives(p, cfg)
-    assert np.array_equal(rt, orep) and np.array_equal(st, ostab)
-    assert np.array_equal(it >= 0, okept)
-    assert np.array_equal(s[it[it >= 0]], orep[it >= 0])
+    for method in (0, 1):
+        rt, gt, pt, st, it = B.find_rep(torch.from_numpy(cfg.view(np.int64)).cuda().view(torch.uint64),
+                                        method=method)
+        rt = rt.cpu().view(torch.int64).numpy().view(np.uint64)
+        pt, st, it = pt.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy()
+        assert np.array_equal(rt, orep) and np.array_equal(st, ostab)
+        assert np.array_equal(it >= 0, okept)
+        assert np.array_equal(s[it[it >= 0]], orep[it >= 0])
+        assert np.array_equal(pt[okept], p.phase_num[og[okept]])
     # H x on sampled rows, fp64 and fp32
     x = w.state_uniform(s, 1804)
     y = B.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()

@@ -61,34 +61,48 @@ def test_worked_examples_on_gpu():
         p = w.chain(6, nsub, n_up=3)
         B = gpu_basis(p)
         s = torch.tensor([50], dtype=torch.uint64, device="cuda")
-        rep, sym, stab, idx = B.find_rep(s)
+        rep, sym, ph, stab, idx = B.find_rep(s)
         assert int(rep.cpu()[0]) == rep_int and int(sym.cpu()[0]) == g_name
         assert int(stab.cpu()[0]) == 1
+        rep2, _, _, stab2, _ = B.find_rep(s, method=1)
+        assert int(rep2.cpu()[0]) == rep_int and int(stab2.cpu()[0]) == 1
 
 
 # ------------------------------------------------------------------ find_rep, exhaustive
+def _two_level_ok(p):
+    n = p.n_sites // p.n_sublat
+    return 2 <= p.n_sublat <= 4 and n <= 11
+
+
+@pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("p", SMALL, ids=_id)
-def test_find_rep_exhaustive(p):
+def test_find_rep_exhaustive(p, method):
+    if method == 1 and not _two_level_ok(p):
+        pytest.skip("two-level search needs 2..4 sublattices of <= 11 sites")
     B = gpu_basis(p)
     states = _sector_states(p.n_sites)
-    rep, sym, stab, idx = B.find_rep(torch.from_numpy(states.view(np.int64)).view(torch.uint64).cuda())
+    rep, sym, ph, stab, idx = B.find_rep(torch.from_numpy(states.view(np.int64)).view(torch.uint64).cuda(),
+                                         method=method)
     rep = rep.cpu().view(torch.int64).numpy().view(np.uint64)
-    sym, stab, idx = sym.cpu().numpy(), stab.cpu().numpy(), idx.cpu().numpy()
+    sym, ph, stab, idx = sym.cpu().numpy(), ph.cpu().numpy(), stab.cpu().numpy(), idx.cpu().numpy()
     orep, og, ostab, okept = oracle.representatives(p, states)
     assert np.array_equal(rep, orep)
     assert np.array_equal(stab, ostab)
-    # the minimising element is unique up to the stabiliser: check g s == rep
-    for g in np.unique(sym):
-        sel = sym == g
-        assert np.array_equal(oracle.apply_sym(p, int(g), states[sel]), orep[sel])
+    if method == 0:
+        # the minimising element is unique up to the stabiliser: check g s == rep
+        for g in np.unique(sym):
+            sel = sym == g
+            assert np.array_equal(oracle.apply_sym(p, int(g), states[sel]), orep[sel])
+        assert np.array_equal(ph, p.phase_num[sym])
+    else:
+        assert np.all(sym == -1)
     ob, _ = oracle.basis(p)
     pos = np.searchsorted(ob, orep)
     in_basis = (pos < ob.size) & (ob[np.minimum(pos, max(ob.size - 1, 0))] == orep) if ob.size else np.zeros(states.size, bool)
     assert np.array_equal(idx >= 0, in_basis)
     assert np.array_equal(idx[in_basis], pos[in_basis])
-    # characters of the two minimisers agree on every surviving representative
-    ph = p.phase_num
-    assert np.array_equal(ph[sym[in_basis]], ph[og[in_basis]])
+    # every minimiser of a surviving representative has the same character: compare it
+    assert np.array_equal(ph[in_basis], p.phase_num[og[in_basis]])
 
 
 # ------------------------------------------------------------------ basis, bit-exact
