@@ -239,6 +239,25 @@ int ed_dot(ed_basis *basis, const void *x, const void *y, int32_t dtype, double 
  */
 int ed_count_terms(const ed_basis *basis, int64_t *n_flip, int64_t *n_offdiag, void *stream);
 
+/*
+ * ed_dot_noalloc -- sum_i conj(x_i) y_i over n DEVICE elements of dtype, in double, like
+ * ed_dot, but without allocating anything and without a basis.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory when they need
+ * the reduction -- a host loop that must not stall the device (cudaMalloc / cudaFree may
+ * synchronise it), or a framework that owns all device memory through its own pool.
+ *   x, y: DEVICE arrays of n elements (caller-owned).  out: DEVICE array of 2 doubles
+ *   (re, im), written by the device; asynchronous on stream.
+ *   n: 0 .. 2^30 (1073741824); larger n is refused with ED_ERR_INVALID.
+ * The block partials live in a fixed 1 MiB array compiled into the library, present on
+ * every device that loads it until the process exits.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the device race on it and must be ordered by the caller (same stream, or
+ * events).  Errors: ED_ERR_INVALID, ED_ERR_CUDA.
+ */
+int ed_dot_noalloc(const void *x, const void *y, int64_t n, int32_t dtype, double *out,
+                   void *stream);
+
 /* ed_last_error -- message of the last failing call on this thread ("" if none). */
 const char *ed_last_error(void);
 

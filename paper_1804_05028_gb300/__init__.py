@@ -26,7 +26,7 @@ LIB_PATH = _build.LIB
 # every function declared in include/sced.h
 SYMBOLS = ["ed_build_basis", "ed_free_basis", "ed_basis_info", "ed_basis_export",
            "ed_find_rep", "ed_apply_H", "ed_apply_H_rows", "ed_apply_H_host", "ed_lanczos",
-           "ed_dot", "ed_count_terms", "ed_last_error", "ed_version"]
+           "ed_dot", "ed_count_terms", "ed_dot_noalloc", "ed_last_error", "ed_version"]
 
 _ERR = {1: "ED_ERR_INVALID", 2: "ED_ERR_UNSTABLE", 3: "ED_ERR_OOM", 4: "ED_ERR_CUDA",
         5: "ED_ERR_TIMEOUT", 6: "ED_ERR_EMPTY", 7: "ED_ERR_UNSUPPORTED"}
@@ -115,6 +115,7 @@ def lib():
             L.ed_lanczos.argtypes = [vp, vp, vp, vp, vp]
             L.ed_dot.argtypes = [vp, vp, vp, i32, vp, vp]
             L.ed_count_terms.argtypes = [vp, vp, vp, vp]
+            L.ed_dot_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
             L.ed_last_error.restype = ctypes.c_char_p
             L.ed_version.restype = ctypes.c_char_p
             _lib = L
@@ -305,6 +306,20 @@ class Basis:
         return {"E0": r.E0, "steps": k, "converged": bool(r.converged), "rq": r.rq,
                 "alpha": alpha[:k].copy(), "beta": beta[:max(k - 1, 0)].copy(),
                 "ms_total": r.ms_total, "ms_apply": r.ms_apply}
+
+
+def dot_noalloc(x, y, out, stream=None):
+    """ed_dot_noalloc: <x, y> into the caller's CUDA float64 tensor ``out`` (2 entries:
+    re, im) without allocating anything -- for callers that cannot allocate device memory
+    at that point (a loop that must not stall the device, or a framework that owns all
+    device memory).  Asynchronous; calls that overlap on the device race on the library's
+    fixed scratch array."""
+    import torch
+    if out.dtype != torch.float64 or out.numel() < 2:
+        raise TypeError("out must be a CUDA float64 tensor of 2 entries")
+    _check(lib().ed_dot_noalloc(_dev(x), _dev(y, x.dtype), x.numel(), _dtype_code(x), _dev(out),
+                                _stream(stream)))
+    return out
 
 
 def build_basis(n_sites, n_sublat, bonds, bond_class, n_classes, perm, phase_num, phase_denom,
