@@ -45,6 +45,7 @@ WORKLOADS = {
     "chain16": ("Heisenberg chain N=16 periodic, Sz=0, C16, k=0", workloads.config_chain16),
 }
 KERNEL_SOURCES = ["paper_1804_05028_gb300/csrc/apply.cu",
+                  "paper_1804_05028_gb300/csrc/apply_fast.cu",
                   "paper_1804_05028_gb300/csrc/sced_internal.cuh"]
 
 
@@ -137,18 +138,23 @@ def alg_bytes(D: int, n_off: int, vec_bytes: int) -> int:
 
 
 def cpu_baseline(p, states, seconds: float, seed: int = 7):
-    """The oracle's matrix-free rows (brute-force representatives) on a sample of rows."""
+    """The oracle's matrix-free rows (brute-force representatives) on a sample of rows,
+    sized to about `seconds` of work on the host cores."""
     import oracle
     rng = np.random.default_rng(seed)
     xf = lambda q: workloads.state_uniform(q, 1804)
-    n = 64
-    oracle.rows(p, states[:16], xf)
-    t0 = time.perf_counter()
-    oracle.rows(p, states[np.sort(rng.choice(states.size, n, replace=False))], xf)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    n = int(min(states.size, max(64, n * seconds / dt)))
+    oracle.rows(p, states[:16], xf)            # load the library, start the thread pool
+    n, dt = 64, 0.0
+    while True:                                # grow the calibration sample to >= 1 s
+        pick = np.sort(rng.choice(states.size, min(n, states.size), replace=False))
+        t0 = time.perf_counter()
+        oracle.rows(p, states[pick], xf)
+        dt = time.perf_counter() - t0
+        if dt >= 1.0 or n >= states.size:
+            break
+        n *= 4
+    n = int(min(states.size, max(64, n * seconds / max(dt, 1e-3))))
     pick = np.sort(rng.choice(states.size, n, replace=False))
-    diag, nt, reps, val = oracle.columns(p, states[pick[:1]])   # warm the library
     t0 = time.perf_counter()
     oracle.rows(p, states[pick], xf)
     dt = time.perf_counter() - t0
@@ -178,9 +184,10 @@ def run_reference(args):
     xf = lambda q: workloads.state_uniform(q, 1804)
     # calibrate rows per step to about one second
     oracle.rows(p, reps[:16], xf)
+    m = min(reps.size, 256)
     t0 = time.perf_counter()
-    oracle.rows(p, reps[:64], xf)
-    per_row = max((time.perf_counter() - t0) / 64, 1e-6)
+    oracle.rows(p, reps[:m], xf)
+    per_row = max((time.perf_counter() - t0) / m, 1e-6)
     n_rows = int(max(16, min(reps.size, 1.0 / per_row)))
     step_rows = [reps[np.sort(rng.choice(reps.size, n_rows, replace=False))] for _ in range(args.warmup + args.steps)]
     for k in range(args.warmup):
