@@ -267,3 +267,17 @@ def test_descriptor_errors():
     B = gpu_basis(w.chain(6, 2, k=1, n_up=3))
     with pytest.raises(ed.EdError):            # complex sector needs a complex vector
         B.apply_H(torch.zeros(B.dim, dtype=torch.float64, device="cuda"))
+
+
+def test_sharded_driver_on_one_gpu():
+    """The row-sharded driver with the CUDA rows (world size 1: no collective runs)."""
+    from paper_1804_05028_gb300.parallel import ShardedOperator, cuda_local_apply, sharded_lanczos
+    p = w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=0.5, n_sublat=4, n_up=8)
+    B = gpu_basis(p)
+    H, bs, _ = oracle.hamiltonian(p)
+    op = ShardedOperator(cuda_local_apply(B), B.dim, 0, 1)
+    x = torch.from_numpy(_x_for(bs, False)).cuda()
+    assert torch.allclose(op.matvec(x), B.apply_H(x), rtol=0, atol=1e-13)
+    e, steps, a, b = sharded_lanczos(op, x.clone())
+    e_ref = np.linalg.eigvalsh(H.toarray())[0]
+    assert abs(e - e_ref) < 1e-10 * abs(e_ref)
