@@ -200,6 +200,9 @@ typedef struct {
   void *work;                 /* optional DEVICE workspace of >= 3 * dim elements of dtype,
                                  caller-owned; when NULL the call allocates its own */
   int64_t work_bytes;         /* size of work in bytes */
+  double tol_residual;        /* > 0: also require the Ritz residual beta_m |s_m| of the lowest
+                                 pair to fall below tol_residual * max(1, |E0|) (for an
+                                 accurate ground state, e.g. derivatives); 0: energy only */
 } ed_lanczos_opts;
 
 typedef struct {
@@ -238,6 +241,18 @@ int ed_dot(ed_basis *basis, const void *x, const void *y, int32_t dtype, double 
  * contributions that apply_H gathers.  HOST outputs; synchronous.
  */
 int ed_count_terms(const ed_basis *basis, int64_t *n_flip, int64_t *n_offdiag, void *stream);
+
+/*
+ * ed_expect_classes -- out[c] = Re <x | H_c | x> for every coupling class c, where H_c is
+ * the class-c part of Eq. 21 with unit exchange (J_c = 1) and anisotropy Jz[c], so that
+ * H = sum_c J_c H_c.  For a normalised ground state psi this is dE0/dJ_c (Hellmann-Feynman
+ * theorem), the derivative the product's adjoint needs.  One pass of the product kernel
+ * with per-class partial sums.
+ *   Jz: HOST [n_classes].  x: DEVICE vector of dim elements, ED_F64 or ED_C128.
+ *   out: HOST [n_classes].  Synchronous.  Errors: ED_ERR_INVALID, ED_ERR_CUDA.
+ */
+int ed_expect_classes(ed_basis *basis, const double *Jz, const void *x, int32_t dtype,
+                      double *out, void *stream);
 
 /*
  * ed_dot_noalloc -- sum_i conj(x_i) y_i over n DEVICE elements of dtype, in double, like

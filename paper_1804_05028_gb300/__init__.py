@@ -26,7 +26,8 @@ LIB_PATH = _build.LIB
 # every function declared in include/sced.h
 SYMBOLS = ["ed_build_basis", "ed_free_basis", "ed_basis_info", "ed_basis_export",
            "ed_find_rep", "ed_apply_H", "ed_apply_H_rows", "ed_apply_H_host", "ed_lanczos",
-           "ed_dot", "ed_count_terms", "ed_dot_noalloc", "ed_last_error", "ed_version"]
+           "ed_dot", "ed_count_terms", "ed_expect_classes", "ed_dot_noalloc", "ed_last_error",
+           "ed_version"]
 
 _ERR = {1: "ED_ERR_INVALID", 2: "ED_ERR_UNSTABLE", 3: "ED_ERR_OOM", 4: "ED_ERR_CUDA",
         5: "ED_ERR_TIMEOUT", 6: "ED_ERR_EMPTY", 7: "ED_ERR_UNSUPPORTED"}
@@ -75,7 +76,7 @@ class _LOpts(ctypes.Structure):
                 ("v0", ctypes.c_void_p), ("psi", ctypes.c_void_p),
                 ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("work", ctypes.c_void_p),
-                ("work_bytes", ctypes.c_int64)]
+                ("work_bytes", ctypes.c_int64), ("tol_residual", ctypes.c_double)]
 
 
 class _LRes(ctypes.Structure):
@@ -116,6 +117,7 @@ def lib():
             L.ed_dot.argtypes = [vp, vp, vp, i32, vp, vp]
             L.ed_count_terms.argtypes = [vp, vp, vp, vp]
             L.ed_dot_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
+            L.ed_expect_classes.argtypes = [vp, vp, vp, i32, vp, vp]
             L.ed_last_error.restype = ctypes.c_char_p
             L.ed_version.restype = ctypes.c_char_p
             _lib = L
@@ -274,13 +276,21 @@ class Basis:
         _check(lib().ed_count_terms(self._h, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
         return a.value, b.value
 
+    def expect_classes(self, x, Jz=None, stream=None):
+        """Re <x|H_c|x> per coupling class c (unit exchange J_c = 1): numpy array."""
+        _, cJz = self._couplings((1.0,) * self.n_classes, Jz)
+        out = (ctypes.c_double * self.n_classes)()
+        _check(lib().ed_expect_classes(self._h, cJz, _dev(x), _dtype_code(x), out,
+                                       _stream(stream)))
+        return np.array(out[:])
+
     def dot(self, x, y, stream=None) -> complex:
         out = (ctypes.c_double * 2)()
         _check(lib().ed_dot(self._h, _dev(x), _dev(y, x.dtype), _dtype_code(x), out, _stream(stream)))
         return complex(out[0], out[1]) if x.is_complex() else out[0]
 
     def lanczos(self, J=None, Jz=None, dtype=None, max_steps=300, fixed_steps=0, tol=1e-13,
-                seed=1805, v0=None, psi=None, work=None, stream=None):
+                seed=1805, v0=None, psi=None, work=None, tol_residual=0.0, stream=None):
         """Lanczos ground-state energy; returns a dict (E0, steps, converged, alpha, beta, ...)."""
         import torch
         if dtype is None:
@@ -292,6 +302,7 @@ class Basis:
         beta = np.zeros(m)
         o = _LOpts()
         o.max_steps, o.fixed_steps, o.tol, o.dtype, o.seed = int(max_steps), int(fixed_steps), float(tol), code, int(seed)
+        o.tol_residual = float(tol_residual)
         o.v0 = _dev(v0, dtype).value if v0 is not None else None
         o.psi = _dev(psi, dtype).value if psi is not None else None
         o.alpha, o.beta = alpha.ctypes.data, beta.ctypes.data

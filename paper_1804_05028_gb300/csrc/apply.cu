@@ -93,7 +93,10 @@ __device__ __forceinline__ void stage(const ApplyParams &P, unsigned char *sm) {
   __syncthreads();
 }
 
-template <typename V, bool kStage>
+// kMode 0: y = H x (and the optional <x, y> partials).  kMode 1: no y; per coupling class
+// c the partial sums of Re <x | H_c x> with unit exchange (P.jh, P.jzq set for J_c = 1)
+// into P.partial[c * gridDim.x + block] (Hellmann-Feynman derivative dE0/dJ_c).
+template <typename V, bool kStage, int kMode>
 __global__ void __launch_bounds__(256) apply_h_kernel(const ApplyParams P) {
   using A = typename Vt<V>::A;
   constexpr bool kC = Vt<V>::cplx;
@@ -115,6 +118,8 @@ __global__ void __launch_bounds__(256) apply_h_kernel(const ApplyParams P) {
   V *y = reinterpret_cast<V *>(P.y);
 
   double dot_re = 0.0, dot_im = 0.0;
+  double cls_dot[kMode == 1 ? ED_MAXCLS : 1];
+  for (int c = 0; c < (kMode == 1 ? ED_MAXCLS : 1); c++) cls_dot[c] = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = P.r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.r1; i += stride) {
     const uint64_t s = __ldg(P.I.basis + i);
@@ -146,10 +151,23 @@ __global__ void __launch_bounds__(256) apply_h_kernel(const ApplyParams P) {
           acc_im += cr * xj.y + ci * xj.x;
         }
       }
-      diag += P.jzq[c] * (double)((b1 - P.cls_off[c]) - 2 * nanti);
+      const double dg = P.jzq[c] * (double)((b1 - P.cls_off[c]) - 2 * nanti);
+      diag += dg;
       row_re += (A)P.jh[c] * acc_re;
       if constexpr (kC) row_im += (A)P.jh[c] * acc_im;
+      if constexpr (kMode == 1) {
+        const double rsd = (double)sq[2 * ti + 1];
+        if constexpr (!kC) {
+          const double xv = (double)x[i];
+          cls_dot[c] += dg * xv * xv + P.jh[c] * rsd * xv * (double)acc_re;
+        } else {
+          const V xv = x[i];
+          cls_dot[c] += dg * ((double)xv.x * xv.x + (double)xv.y * xv.y) +
+                        P.jh[c] * rsd * ((double)xv.x * acc_re + (double)xv.y * acc_im);
+        }
+      }
     }
+    if constexpr (kMode == 1) continue;
     const A rs = sq[2 * ti + 1];
     if constexpr (!kC) {
       const V xi = x[i];
@@ -168,15 +186,20 @@ __global__ void __launch_bounds__(256) apply_h_kernel(const ApplyParams P) {
       }
     }
   }
+  if constexpr (kMode == 1) {
+    for (int c = 0; c < P.n_classes; c++)
+      block_reduce_store<double>(cls_dot[c], P.partial, c * gridDim.x + blockIdx.x);
+    return;
+  }
   if (P.partial) {
     block_reduce_store<double>(dot_re, P.partial, blockIdx.x);
     if (kC) block_reduce_store<double>(dot_im, P.partial, gridDim.x + blockIdx.x);
   }
 }
 
-template <typename V, bool kStage>
+template <typename V, bool kStage, int kMode = 0>
 int launch_apply_t(const ApplyParams &P, int grid, cudaStream_t st) {
-  auto k = apply_h_kernel<V, kStage>;
+  auto k = apply_h_kernel<V, kStage, kMode>;
   if (P.smem_bytes > 48 * 1024)
     ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
   k<<<grid, 256, P.smem_bytes, st>>>(P);
@@ -322,10 +345,10 @@ static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const void *x,
                     void *y, int dtype, int64_t r0, int64_t r1, double *partial,
-                    cudaStream_t st) {
+                    cudaStream_t st, int mode) {
   if (r1 <= r0) return ED_OK;
   if (!getenv("SCED_GENERIC_APPLY")) {
-    const int rc = ed_launch_apply_fast(B, J, Jz, x, y, dtype, r0, r1, partial, st);
+    const int rc = ed_launch_apply_fast(B, J, Jz, x, y, dtype, r0, r1, partial, st, mode);
     if (rc != ED_ERR_UNSUPPORTED) return rc;
   }
   ApplyParams P{};
@@ -378,6 +401,12 @@ int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const 
   if (partial && grid > B->n_partial / 2) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
   B->last_apply_grid = grid;
   const bool sg = P.stage_tables != 0;
+  if (mode == 1) {
+    if (!partial || B->n_classes * grid > B->n_partial) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
+    if (dtype == ED_F64) return sg ? launch_apply_t<double, true, 1>(P, grid, st) : launch_apply_t<double, false, 1>(P, grid, st);
+    if (dtype == ED_C128) return sg ? launch_apply_t<double2, true, 1>(P, grid, st) : launch_apply_t<double2, false, 1>(P, grid, st);
+    return ed_fail(ED_ERR_INVALID, "class expectations need fp64 vectors");
+  }
   switch (dtype) {
     case ED_F64: return sg ? launch_apply_t<double, true>(P, grid, st) : launch_apply_t<double, false>(P, grid, st);
     case ED_F32: return sg ? launch_apply_t<float, true>(P, grid, st) : launch_apply_t<float, false>(P, grid, st);

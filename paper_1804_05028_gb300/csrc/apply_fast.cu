@@ -240,7 +240,9 @@ __device__ __forceinline__ int64_t lookup_two(const Sm2 &S, const TwoParams &P, 
   return -1;
 }
 
-template <typename V, int NSUB, bool kE2>
+// kMode 0: y = H x (and optional <x, y> partials); kMode 1: per coupling class the
+// partial sums of Re <x | H_c x> with unit exchange, into partial[c * grid + block].
+template <typename V, int NSUB, bool kE2, int kMode>
 __global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : 2) apply_two_kernel(const TwoParams P) {
   using A = typename Vf<V>::A;
   constexpr bool kC = Vf<V>::cplx;
@@ -256,6 +258,8 @@ __global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : 2) apply_two_kerne
   const uint32_t bmask = (1u << n) - 1u;
 
   double dot_re = 0.0, dot_im = 0.0;
+  double cls_dot[kMode == 1 ? ED_MAXCLS : 1];
+  for (int c = 0; c < (kMode == 1 ? ED_MAXCLS : 1); c++) cls_dot[c] = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = P.r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.r1; i += stride) {
     const uint64_t s = __ldg(P.basis + i);
@@ -316,10 +320,22 @@ __global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : 2) apply_two_kerne
           }
         }
       }
-      diag += P.jzq[c] * (double)(P.nb_cls[c] - 2 * nanti);
+      const double dg = P.jzq[c] * (double)(P.nb_cls[c] - 2 * nanti);
+      diag += dg;
       row_re += P.jh[c] * ((double)acc_re + (double)lo_re);
       if (kC) row_im += P.jh[c] * (double)acc_im;
+      if constexpr (kMode == 1) {
+        if constexpr (!kC) {
+          const double xv = (double)x[i];
+          cls_dot[c] += dg * xv * xv + P.jh[c] * rsd[ti] * xv * ((double)acc_re + (double)lo_re);
+        } else {
+          const V xv = x[i];
+          cls_dot[c] += dg * ((double)xv.x * xv.x + (double)xv.y * xv.y) +
+                        P.jh[c] * rsd[ti] * ((double)xv.x * acc_re + (double)xv.y * acc_im);
+        }
+      }
     }
+    if constexpr (kMode == 1) continue;
     const double rs = rsd[ti];
     if constexpr (!kC) {
       const double xi = (double)x[i];
@@ -341,8 +357,9 @@ __global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : 2) apply_two_kerne
   if (P.partial) {
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int part = 0; part < (kC ? 2 : 1); part++) {
-      double d = part ? dot_im : dot_re;
+    const int nparts = kMode == 1 ? P.n_classes : (kC ? 2 : 1);
+    for (int part = 0; part < nparts; part++) {
+      double d = kMode == 1 ? cls_dot[part] : (part ? dot_im : dot_re);
       for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xFFFFFFFFu, d, o);
       __syncthreads();
       if (lane == 0) red[wid] = d;
@@ -435,14 +452,14 @@ int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, T
 
 // e2 staged: one 1024-thread CTA per SM (the tables take most of shared memory);
 // otherwise two 512-thread CTAs per SM.  Both give 32 warps per SM at 64 registers.
-template <typename V, int NSUB>
+template <typename V, int NSUB, int kMode = 0>
 int launch_t(const TwoParams &P, bool e2, int grid, cudaStream_t st) {
   if (e2) {
-    auto k = apply_two_kernel<V, NSUB, true>;
+    auto k = apply_two_kernel<V, NSUB, true, kMode>;
     ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
     k<<<grid, 1024, P.smem_bytes, st>>>(P);
   } else {
-    auto k = apply_two_kernel<V, NSUB, false>;
+    auto k = apply_two_kernel<V, NSUB, false, kMode>;
     ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
     k<<<grid, 512, P.smem_bytes, st>>>(P);
   }
@@ -450,12 +467,12 @@ int launch_t(const TwoParams &P, bool e2, int grid, cudaStream_t st) {
   return ED_OK;
 }
 
-template <typename V>
+template <typename V, int kMode = 0>
 int launch_v(const TwoParams &P, bool e2, int nsub, int grid, cudaStream_t st) {
   switch (nsub) {
-    case 2: return launch_t<V, 2>(P, e2, grid, st);
-    case 3: return launch_t<V, 3>(P, e2, grid, st);
-    case 4: return launch_t<V, 4>(P, e2, grid, st);
+    case 2: return launch_t<V, 2, kMode>(P, e2, grid, st);
+    case 3: return launch_t<V, 3, kMode>(P, e2, grid, st);
+    case 4: return launch_t<V, 4, kMode>(P, e2, grid, st);
   }
   return ED_ERR_UNSUPPORTED;
 }
@@ -466,7 +483,7 @@ int launch_v(const TwoParams &P, bool e2, int nsub, int grid, cudaStream_t st) {
 // |G| <= 4096); returns ED_ERR_UNSUPPORTED otherwise (the caller uses the generic kernel).
 int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
                          void *y, int dtype, int64_t r0, int64_t r1, double *partial,
-                         cudaStream_t st) {
+                         cudaStream_t st, int mode) {
   TwoParams P;
   bool e2 = true;
   int rc = make_params(B, J, Jz, e2, P);
@@ -480,6 +497,12 @@ int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, c
   if (grid < 1) grid = 1;
   if (partial && grid > B->n_partial / 2) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
   B->last_apply_grid = grid;
+  if (mode == 1) {
+    if (!partial || B->n_classes * grid > B->n_partial) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
+    if (dtype == ED_F64) return launch_v<double, 1>(P, e2, B->nsub, grid, st);
+    if (dtype == ED_C128) return launch_v<double2, 1>(P, e2, B->nsub, grid, st);
+    return ed_fail(ED_ERR_INVALID, "class expectations need fp64 vectors");
+  }
   switch (dtype) {
     case ED_F64: return launch_v<double>(P, e2, B->nsub, grid, st);
     case ED_F32: return launch_v<float>(P, e2, B->nsub, grid, st);

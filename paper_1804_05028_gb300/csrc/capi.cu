@@ -457,7 +457,7 @@ extern "C" int ed_build_basis(const ed_lattice *L, const ed_group *G, const ed_i
   if ((rc = build_tables(B, st))) { free_all(B); delete B; return rc; }
   const int bucket = (opts && opts->bucket_target > 0) ? opts->bucket_target : 4;
   if ((rc = ed_build_device(B, st, bucket))) { free_all(B); delete B; return rc; }
-  B->n_partial = 2 * B->sm_count * 8;
+  B->n_partial = ED_MAXCLS * B->sm_count * 8;   // per-class partials of the widest grid
   if (cudaMalloc(&B->d_partial, (size_t)B->n_partial * 8) != cudaSuccess ||
       cudaMallocHost(&B->h_partial, (size_t)B->n_partial * 8) != cudaSuccess) {
     cudaGetLastError();
@@ -598,6 +598,30 @@ extern "C" int ed_count_terms(const ed_basis *B, int64_t *n_flip, int64_t *n_off
   return ED_OK;
 }
 
+extern "C" int ed_expect_classes(ed_basis *B, const double *Jz, const void *x, int32_t dtype,
+                                 double *out, void *stream) {
+  if (!B || !Jz || !out) return ed_fail(ED_ERR_INVALID, "null argument");
+  if (dtype != ED_F64 && dtype != ED_C128) return ed_fail(ED_ERR_INVALID, "needs fp64 vectors");
+  int rc = check_dtype(B, dtype);
+  if (rc) return rc;
+  for (int c = 0; c < B->n_classes; c++) out[c] = 0.0;
+  if (B->D == 0) return ED_OK;
+  if (!x) return ed_fail(ED_ERR_INVALID, "null vector");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> unit(B->n_classes, 1.0);
+  if ((rc = ed_launch_apply(B, unit.data(), Jz, x, nullptr, dtype, 0, B->D, B->d_partial, st, 1))) return rc;
+  const int g = B->last_apply_grid;
+  ED_CK(cudaMemcpyAsync(B->h_partial, B->d_partial, (size_t)B->n_classes * g * 8,
+                        cudaMemcpyDeviceToHost, st));
+  ED_CK(cudaStreamSynchronize(st));
+  for (int c = 0; c < B->n_classes; c++) {
+    double a = 0;
+    for (int k = 0; k < g; k++) a += B->h_partial[(size_t)c * g + k];
+    out[c] = a;
+  }
+  return ED_OK;
+}
+
 // --------------------------------------------------------------------------------------
 // Lanczos
 // --------------------------------------------------------------------------------------
@@ -666,8 +690,15 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
       *steps = j + 1;
       bool stop = false;
       if (!fixed && have_old && std::fabs(e - e_old) < tol * std::max(1.0, std::fabs(e))) {
-        *converged = 1;
-        stop = true;
+        bool res_ok = true;
+        if (o->tol_residual > 0) {   // residual of the lowest Ritz pair: beta_m |s_m|
+          const std::vector<double> s = tri_eigvec(alpha, beta, (int)alpha.size(), e);
+          res_ok = b * std::fabs(s.back()) < o->tol_residual * std::max(1.0, std::fabs(e));
+        }
+        if (res_ok) {
+          *converged = 1;
+          stop = true;
+        }
       }
       if (b < 1e-14 * std::max(1.0, std::fabs(a)) || (int64_t)alpha.size() >= B->D) {
         *converged = 1;   // invariant subspace: T holds exact eigenvalues

@@ -281,8 +281,11 @@ int ed_cuda_fail(cudaError_t e, const char *what);
 
 // kernels.cu / basis.cu entry points used by capi.cu
 int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target);
+// mode 0: y = H x (partial: optional <x, y> block partials); mode 1: per-class block partials
+// of Re <x | H_c x> (J, Jz: unit couplings) into partial[c * grid + block], y unused
 int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const void *x, void *y,
-                    int dtype, int64_t r0, int64_t r1, double *partial, cudaStream_t st);
+                    int dtype, int64_t r0, int64_t r1, double *partial, cudaStream_t st,
+                    int mode = 0);
 int ed_launch_find_rep(const ed_basis *B, const uint64_t *states, int64_t n, uint64_t *rep,
                        int32_t *sym, int32_t *phase, int32_t *stab, int64_t *index,
                        cudaStream_t st);
@@ -298,6 +301,6 @@ int ed_launch_axpy(const ed_basis *B, void *y, const void *x, double a, int dtyp
 int ed_launch_start(const ed_basis *B, void *v, uint64_t seed, int dtype, cudaStream_t st);
 int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
                          void *y, int dtype, int64_t r0, int64_t r1, double *partial,
-                         cudaStream_t st);
+                         cudaStream_t st, int mode);
 int ed_launch_count(const ed_basis *B, unsigned long long *d_out, cudaStream_t st);
 int ed_launch_copy(const ed_basis *B, void *dst, const void *src, int dtype, cudaStream_t st);

@@ -1,0 +1,94 @@
+"""dE0/dJ through the adjoint product: class-resolved expectations against the oracle,
+torch.autograd against central finite differences (h = 1e-4, fp64) and against the
+Hellmann-Feynman value from the oracle's dense ground state."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _ed():
+    import paper_1804_05028_gb300 as ed
+    return ed
+
+
+def _unit(p, c, Jz=None):
+    J = [0.0] * p.n_classes
+    J[c] = 1.0
+    return p.with_couplings(J, Jz)
+
+
+@pytest.mark.parametrize("p", [
+    w.chain(16, 2, k=3, n_up=8, Jz=0.7),
+    w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=0.5, n_sublat=4, n_up=8),
+    w.square_torus(4, momentum=(1, 1), point_irrep=0, J2=0.5, n_sublat=1, n_up=6),
+    w.square_torus(4, momentum=(1, 0), point_irrep=1, J2=0.5, n_sublat=2, n_up=8),
+], ids=lambda p: p.name)
+def test_class_expectations_match_oracle(p):
+    B = _ed().build_basis_from(p)
+    bs, _ = B.export()
+    x = w.state_uniform(bs, 11)
+    if not p.is_real():
+        x = x + 1j * w.state_uniform(bs, 12)
+    xt = torch.from_numpy(x).cuda()
+    got = B.expect_classes(xt)
+    for c in range(p.n_classes):
+        Hc, _, _ = oracle.hamiltonian(_unit(p, c, p.Jz))
+        ref = np.vdot(x, Hc @ x).real
+        assert abs(got[c] - ref) <= 1e-12 * max(1.0, abs(ref))
+    # the classes add up to the full product
+    J = np.array(p.J)
+    full = B.dot(xt, B.apply_H(xt))
+    assert abs(np.dot(J, got) - np.real(full)) <= 1e-11 * abs(full)
+
+
+@pytest.mark.parametrize("J2", [0.40, 0.50, 0.60])
+def test_dE0_dJ_autograd_fd_and_hellmann_feynman(J2):
+    from paper_1804_05028_gb300.autograd import ground_state_energy
+    p = w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=J2, n_sublat=4, n_up=8)
+    B = _ed().build_basis_from(p)
+    J = torch.tensor([1.0, J2], dtype=torch.float64, requires_grad=True)
+    E = ground_state_energy(B, J)
+    E.backward()
+    g = J.grad.numpy()
+    # central finite differences
+    h = 1e-4
+    fd = []
+    for c in range(2):
+        e = []
+        for sgn in (1, -1):
+            Jc = [1.0, J2]
+            Jc[c] += sgn * h
+            e.append(B.lanczos(J=Jc)["E0"])
+        fd.append((e[0] - e[1]) / (2 * h))
+    # the h = 1e-4 central stencil has a truncation error of h^2 |d3E/dJ3| / 6, ~1e-7 here
+    assert np.allclose(g, fd, rtol=0, atol=1e-6)
+    # Hellmann-Feynman from the oracle's dense ground state
+    H, bs, _ = oracle.hamiltonian(p)
+    ev, vec = np.linalg.eigh(H.toarray())
+    psi = vec[:, 0]
+    hf = [psi @ (oracle.hamiltonian(_unit(p, c))[0] @ psi) for c in range(2)]
+    assert np.allclose(g, hf, rtol=0, atol=1e-9)
+    assert abs(E.item() - ev[0]) < 1e-10 * abs(ev[0])
+
+
+def test_dE0_dJ_square36_j2_half():
+    """Full 6x6 J1-J2 Gamma-A1 sector at J2 = 0.5: autograd against central differences."""
+    from paper_1804_05028_gb300.autograd import ground_state_energy
+    p = w.config_square36(0.5)
+    B = _ed().build_basis_from(p)
+    J = torch.tensor([1.0, 0.5], dtype=torch.float64, requires_grad=True)
+    E = ground_state_energy(B, J)
+    E.backward()
+    g = J.grad.numpy()
+    h = 1e-4
+    Jp = [1.0, 0.5 + h]
+    Jm = [1.0, 0.5 - h]
+    fd2 = (B.lanczos(J=Jp)["E0"] - B.lanczos(J=Jm)["E0"]) / (2 * h)
+    assert abs(g[1] - fd2) < 2e-6
+    # Euler: E0 is homogeneous of degree 1 in J, so sum_c J_c dE0/dJ_c = E0
+    assert abs(1.0 * g[0] + 0.5 * g[1] - E.item()) < 1e-8 * abs(E.item())
