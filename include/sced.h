@@ -59,7 +59,8 @@ extern "C" {
 typedef struct {
   int32_t n_sites;            /* N, 1..64 */
   int32_t n_sublat;           /* number of sublattices, divides N; N/n_sublat <= 20 when > 1,
-                                 N <= 24 when 1 (one full lookup table, Sec. III) */
+                                 N <= 26 when 1 (the whole lookup table of Sec. III, built
+                                 on the device: 2^N entries of 8 bytes) */
   int32_t n_bonds;            /* 1..4096 */
   int32_t n_classes;          /* coupling classes, 1..8 */
   const int32_t *bonds;       /* [n_bonds][2] site labels, distinct */
@@ -78,13 +79,18 @@ typedef struct {
   const int32_t *phase_num;   /* [n_sym] */
 } ed_irrep;
 
+typedef struct ed_basis ed_basis;   /* opaque; owns (or shares) every device table it uses */
+
 /* Tuning of the basis and its index; pass NULL for defaults. */
 typedef struct {
   int32_t bucket_target;      /* average states per Limits bucket (default 4) */
-  int32_t reserved[7];
+  int32_t reserved0;
+  const ed_basis *share_tables; /* optional: a basis of the same lattice and group whose
+                                   one-sublattice table (n_sublat == 1) is reused instead of
+                                   building a copy; it stays valid until every basis that
+                                   uses it is freed */
+  int64_t reserved[2];
 } ed_basis_opts;
-
-typedef struct ed_basis ed_basis;   /* opaque; owns every device table it creates */
 
 typedef struct {
   int64_t dim;                /* D, number of basis states */
@@ -253,6 +259,38 @@ int ed_count_terms(const ed_basis *basis, int64_t *n_flip, int64_t *n_offdiag, v
  */
 int ed_expect_classes(ed_basis *basis, const double *Jz, const void *x, int32_t dtype,
                       double *out, void *stream);
+
+/*
+ * Batched product over many sectors (the uneven-sector workload): sectors of one lattice
+ * (same sites, bonds, classes) that differ in group, irrep and n_up, each applied to k
+ * vectors at once, all in one persistent launch.  Work items (sector, block of rows) are
+ * taken from a device counter (atomicAdd; no CTA waits on another), so sectors of any size
+ * mix in one launch.  Each exchange term is searched (Alg. 2) and looked up (Sec. IV) once
+ * and applied to the k vectors, stored row-major: x[s][i*k + v].  Vectors are fp32 for real
+ * sectors and complex fp32 (interleaved) for sectors with complex characters.
+ */
+typedef struct ed_batch ed_batch;
+
+/* ed_batch_create -- a batch of n bases (kept by reference: they must outlive the batch),
+ * couplings J, Jz (HOST [n_classes]) and block width k in {1, 2, 4, 8}. */
+int ed_batch_create(ed_basis *const *bases, int32_t n, const double *J, const double *Jz,
+                    int32_t k, ed_batch **out);
+
+/* ed_batch_set_vectors -- DEVICE input / output vectors per sector (HOST arrays of n device
+ * pointers; x[s], y[s] hold dim_s * k elements of fp32 or complex fp32).  Synchronous. */
+int ed_batch_set_vectors(ed_batch *batch, void *const *x, void *const *y);
+
+/* ed_batch_apply -- y[s] = H_s x[s] for every sector, in one launch on stream.  The first call
+ * times a few work-item sizes (rows per item) and keeps the fastest, then captures the
+ * counter reset and the launch in a CUDA graph that later calls replay.  Asynchronous
+ * after the first call. */
+int ed_batch_apply(ed_batch *batch, void *stream);
+
+/* ed_batch_info -- rows per work item chosen by the first ed_batch_apply, and item count. */
+int ed_batch_info(const ed_batch *batch, int32_t *rows_per_item, int64_t *n_items);
+
+/* ed_batch_free -- release the batch (not its bases). */
+void ed_batch_free(ed_batch *batch);
 
 /*
  * ed_dot_noalloc -- sum_i conj(x_i) y_i over n DEVICE elements of dtype, in double, like

@@ -18,16 +18,17 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["lib", "build", "build_basis", "Basis", "EdError", "F64", "F32", "C128", "C64",
-           "LIB_PATH", "SYMBOLS"]
+__all__ = ["lib", "build", "build_basis", "build_basis_from", "Basis", "Batch", "EdError",
+           "F64", "F32", "C128", "C64", "LIB_PATH", "SYMBOLS", "build_sectors", "dot_noalloc"]
 
 F64, F32, C128, C64 = 0, 1, 2, 3
 LIB_PATH = _build.LIB
 # every function declared in include/sced.h
 SYMBOLS = ["ed_build_basis", "ed_free_basis", "ed_basis_info", "ed_basis_export",
            "ed_find_rep", "ed_apply_H", "ed_apply_H_rows", "ed_apply_H_host", "ed_lanczos",
-           "ed_dot", "ed_count_terms", "ed_expect_classes", "ed_dot_noalloc", "ed_last_error",
-           "ed_version"]
+           "ed_dot", "ed_count_terms", "ed_expect_classes", "ed_dot_noalloc", "ed_batch_create",
+           "ed_batch_set_vectors", "ed_batch_apply", "ed_batch_info", "ed_batch_free",
+           "ed_last_error", "ed_version"]
 
 _ERR = {1: "ED_ERR_INVALID", 2: "ED_ERR_UNSTABLE", 3: "ED_ERR_OOM", 4: "ED_ERR_CUDA",
         5: "ED_ERR_TIMEOUT", 6: "ED_ERR_EMPTY", 7: "ED_ERR_UNSUPPORTED"}
@@ -54,7 +55,8 @@ class _Irrep(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("bucket_target", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("bucket_target", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("share_tables", ctypes.c_void_p), ("reserved", ctypes.c_int64 * 2)]
 
 
 class _Info(ctypes.Structure):
@@ -118,6 +120,12 @@ def lib():
             L.ed_count_terms.argtypes = [vp, vp, vp, vp]
             L.ed_dot_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
             L.ed_expect_classes.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.ed_batch_create.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(vp)]
+            L.ed_batch_set_vectors.argtypes = [vp, vp, vp]
+            L.ed_batch_apply.argtypes = [vp, vp]
+            L.ed_batch_info.argtypes = [vp, vp, vp]
+            L.ed_batch_free.argtypes = [vp]
+            L.ed_batch_free.restype = None
             L.ed_last_error.restype = ctypes.c_char_p
             L.ed_version.restype = ctypes.c_char_p
             _lib = L
@@ -319,6 +327,45 @@ class Basis:
                 "ms_total": r.ms_total, "ms_apply": r.ms_apply}
 
 
+class Batch:
+    """Many sectors of one lattice in one persistent launch, each with k vectors
+    (ed_batch_*).  Vectors are CUDA float32 (real sectors) or complex64 tensors holding
+    dim * k values row-major ([dim][k])."""
+
+    def __init__(self, bases, k=1, J=None, Jz=None):
+        self.bases = list(bases)          # the batch refers to them: keep them alive
+        b0 = self.bases[0]
+        cJ, cJz = b0._couplings(J, Jz)
+        arr = (ctypes.c_void_p * len(self.bases))(*[b._h for b in self.bases])
+        h = ctypes.c_void_p()
+        _check(lib().ed_batch_create(arr, len(self.bases), cJ, cJz, int(k), ctypes.byref(h)))
+        self._h, self.k = h, int(k)
+
+    def set_vectors(self, xs, ys):
+        px = (ctypes.c_void_p * len(xs))(*[t.data_ptr() if t.numel() else None for t in xs])
+        py = (ctypes.c_void_p * len(ys))(*[t.data_ptr() if t.numel() else None for t in ys])
+        _check(lib().ed_batch_set_vectors(self._h, px, py))
+        self._keep = (xs, ys)
+
+    def apply(self, stream=None):
+        _check(lib().ed_batch_apply(self._h, _stream(stream)))
+
+    def info(self):
+        r, n = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().ed_batch_info(self._h, ctypes.byref(r), ctypes.byref(n)))
+        return {"rows_per_item": r.value, "n_items": n.value}
+
+    def close(self):
+        if self._h:
+            lib().ed_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h and _lib is not None:
+            _lib.ed_batch_free(h)
+
+
 def dot_noalloc(x, y, out, stream=None):
     """ed_dot_noalloc: <x, y> into the caller's CUDA float64 tensor ``out`` (2 entries:
     re, im) without allocating anything -- for callers that cannot allocate device memory
@@ -334,7 +381,7 @@ def dot_noalloc(x, y, out, stream=None):
 
 
 def build_basis(n_sites, n_sublat, bonds, bond_class, n_classes, perm, phase_num, phase_denom,
-                n_up, J=None, Jz=None, bucket_target=None, stream=None) -> Basis:
+                n_up, J=None, Jz=None, bucket_target=None, share_tables=None, stream=None) -> Basis:
     """Validate a sector, build the sublattice tables and the basis on the current device."""
     bonds = np.ascontiguousarray(bonds, dtype=np.int32)
     bcls = np.ascontiguousarray(bond_class, dtype=np.int32)
@@ -346,6 +393,7 @@ def build_basis(n_sites, n_sublat, bonds, bond_class, n_classes, perm, phase_num
     R = _Irrep(int(phase_denom), pnum.ctypes.data)
     opts = _Opts()
     opts.bucket_target = int(bucket_target or 0)
+    opts.share_tables = share_tables._h if share_tables is not None else None
     h = ctypes.c_void_p()
     _check(lib().ed_build_basis(ctypes.byref(L), ctypes.byref(G), ctypes.byref(R), int(n_up),
                                 ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
@@ -357,3 +405,17 @@ def build_basis_from(problem, **kw) -> Basis:
     p = problem
     return build_basis(p.n_sites, p.n_sublat, p.bonds, p.bond_class, p.n_classes, p.perm,
                        p.phase_num, p.phase_denom, p.n_up, J=p.J, Jz=p.Jz, **kw)
+
+
+def build_sectors(problems, **kw):
+    """build_basis_from for many sectors, sharing the one-sublattice table between sectors
+    whose lattice and group coincide (the table depends on the group only)."""
+    out, first_of_group = [], {}
+    for p in problems:
+        key = (p.n_sites, p.n_sublat, np.asarray(p.perm).tobytes())
+        share = first_of_group.get(key) if p.n_sublat == 1 else None
+        B = build_basis_from(p, share_tables=share, **kw)
+        if p.n_sublat == 1 and key not in first_of_group:
+            first_of_group[key] = B
+        out.append(B)
+    return out

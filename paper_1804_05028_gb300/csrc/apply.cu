@@ -381,7 +381,9 @@ int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const 
   const size_t rest = align16((size_t)B->n_bonds * 2) + align16((size_t)(B->nsym + 1) * 2 * abytes) +
                       align16((size_t)B->denom * 2 * abytes);
   const size_t kMaxSmem = 200 * 1024;
-  P.stage_tables = (tab_bytes + rest <= kMaxSmem) ? 1 : 0;
+  // a one-sublattice split reads the whole table from global memory and has no
+  // Rep/Sym/dest tables to stage
+  P.stage_tables = (!B->T.full && tab_bytes + rest <= kMaxSmem) ? 1 : 0;
   P.sym_list_bytes = (uint32_t)(B->sym_list_len * 2);
   if (P.stage_tables) {
     P.off_rep = (uint32_t)off; off += align16((size_t)B->nsub * nn * 4);

@@ -265,6 +265,33 @@ __global__ void make_postfix(const uint64_t *basis, int64_t D, uint64_t mask, PT
     post[i] = (PT)(basis[i] & mask);
 }
 
+// The whole lookup table of a one-sublattice split: every configuration s < 2^N gets its
+// representative (Eq. 4, every group element applied), the first minimising element and
+// the number of minimisers.  pbit[g*N + b] is the bit that g carries bit b to.
+__global__ void full_table_kernel(const uint8_t *pbit, int N, int nsym, uint64_t *out) {
+  extern __shared__ uint8_t sp[];
+  for (int k = threadIdx.x; k < nsym * N; k += blockDim.x) sp[k] = pbit[k];
+  __syncthreads();
+  const uint64_t total = 1ULL << N;
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t best = ~0ULL;
+    uint32_t gb = 0, cnt = 0;
+    for (int g = 0; g < nsym; g++) {
+      const uint8_t *pg = sp + g * N;
+      uint64_t v = 0, m = s;
+      while (m) {
+        const int b = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        v |= 1ULL << pg[b];
+      }
+      if (v < best) { best = v; gb = g; cnt = 1; }
+      else if (v == best) cnt++;
+    }
+    out[s] = best | ((uint64_t)gb << 32) | ((uint64_t)cnt << 48);
+  }
+}
+
 uint64_t binom_host(int n, int k) {
   if (k < 0 || k > n) return 0;
   uint64_t r = 1;
@@ -273,6 +300,19 @@ uint64_t binom_host(int n, int k) {
 }
 
 }  // namespace
+
+int ed_build_full_table(const uint8_t *d_pbit, int N, int nsym, uint64_t *out, cudaStream_t st) {
+  const size_t sm = (size_t)nsym * N;
+  if (sm > 200 * 1024) return ed_fail(ED_ERR_UNSUPPORTED, "group too large for the one-block table");
+  if (sm > 48 * 1024)
+    ED_CK(cudaFuncSetAttribute(full_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int dev = 0, nsm = 0;
+  ED_CK(cudaGetDevice(&dev));
+  ED_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  full_table_kernel<<<nsm * 8, 256, sm, st>>>(d_pbit, N, nsym, out);
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
 
 // Build Basis, |Stab| and the index on the device.  Tables (B->T) must be in place.
 int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target) {

@@ -1,0 +1,333 @@
+// batch.cu -- the product over many symmetry sectors at once, with block vectors.
+//
+// A batch holds sectors of one lattice (same sites, bonds and couplings) that differ in
+// symmetry group, irrep and n_up, and so in dimension (from 0 to ~2e5 on the 5x5 torus).
+// One persistent launch covers all of them: every CTA takes work items -- (sector,
+// block of consecutive rows) -- from a device counter with atomicAdd until none are
+// left, so uneven sectors balance themselves and no CTA waits on another.  Each row's
+// exchange terms go through the representative search and the Limits lookup once and
+// are applied to k vectors stored row-major ([D][k], so the k values of a gathered row
+// are contiguous), amortising the search over the block.  Vectors are fp32 for real
+// sectors and complex fp32 for sectors with complex characters.  After the first call
+// the counter reset and the launch are replayed from a captured CUDA graph.  The number
+// of rows per work item is picked by timing a few candidates on the first call.
+#include "sced_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+struct BatchSector {
+  DevTables T;
+  DevIndex I;
+  const double *sqrt_tab, *rsqrt_tab, *cs;
+  const void *x;
+  void *y;
+  int64_t D;
+  int64_t item0;     // first work item of this sector
+  int cplx;
+  int pad;
+};
+
+struct ed_batch {
+  int n = 0, k = 1, n_classes = 0, n_bonds = 0;
+  std::vector<ed_basis *> bases;
+  std::vector<BatchSector> host;
+  BatchSector *d_sec = nullptr;
+  int64_t *d_item0 = nullptr;
+  unsigned long long *d_counter = nullptr;
+  uint8_t *d_bond = nullptr;
+  int cls_off[ED_MAXCLS + 1];
+  double jh[ED_MAXCLS], jzq[ED_MAXCLS];
+  int rows_per_item = 0;   // chosen tile
+  int64_t n_items = 0;
+  int sm_count = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  bool vectors_set = false;
+};
+
+namespace {
+
+struct BatchParams {
+  const BatchSector *sec;
+  const int64_t *item0;
+  int n_sec;
+  int64_t n_items;
+  int rows_per_item;
+  unsigned long long *counter;
+  const uint8_t *bond;
+  int n_classes;
+  int cls_off[ED_MAXCLS + 1];
+  float jh[ED_MAXCLS], jzq[ED_MAXCLS];
+};
+
+__device__ __forceinline__ int sector_of(const BatchParams &P, int64_t item) {
+  int lo = 0, hi = P.n_sec - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.item0[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) batch_kernel(const BatchParams P) {
+  __shared__ BatchSector S;
+  __shared__ int64_t item_s;
+  __shared__ uint8_t bond_s[2 * ED_MAXBONDS / 8];
+  const int nb = P.cls_off[P.n_classes];
+  for (int q = threadIdx.x; q < 2 * nb; q += blockDim.x) bond_s[q] = P.bond[q];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item_s = (int64_t)atomicAdd(P.counter, 1ULL);
+    __syncthreads();
+    const int64_t item = item_s;
+    if (item >= P.n_items) break;
+    const int sid = sector_of(P, item);
+    if (threadIdx.x == 0) S = P.sec[sid];
+    __syncthreads();
+    for (int64_t i = (item - S.item0) * P.rows_per_item + threadIdx.x;
+         i < S.D && i < (item - S.item0 + 1) * P.rows_per_item; i += blockDim.x) {
+      const uint64_t s = __ldg(S.I.basis + i);
+      const int ti = __ldg(S.I.stab + i);
+      float yr[K], yi[K];
+#pragma unroll
+      for (int v = 0; v < K; v++) { yr[v] = 0.f; yi[v] = 0.f; }
+      float diag = 0.f;
+      for (int c = 0; c < P.n_classes; c++) {
+        float ar[K], ai[K];
+#pragma unroll
+        for (int v = 0; v < K; v++) { ar[v] = 0.f; ai[v] = 0.f; }
+        int nanti = 0;
+        for (int b = P.cls_off[c]; b < P.cls_off[c + 1]; b++) {
+          const int pa = bond_s[2 * b], pb = bond_s[2 * b + 1];
+          if ((((s >> pa) ^ (s >> pb)) & 1ULL) == 0) continue;
+          nanti++;
+          const RepOut R = find_rep(S.T, S.T.rep, S.T.sym_off, S.T.sym_list, S.T.dest, S.T.phase,
+                                    s ^ ((1ULL << pa) | (1ULL << pb)));
+          if (R.mixed) continue;
+          const int64_t j = lookup_index(S.I, R.rep);
+          if (j < 0) continue;
+          const float w = (float)S.sqrt_tab[R.t];
+          const int ph = S.T.phase[R.g];
+          if (!S.cplx) {
+            const float sg = ph == 0 ? w : -w;
+            const float *xr = reinterpret_cast<const float *>(S.x) + j * K;
+            if constexpr (K % 4 == 0) {
+#pragma unroll
+              for (int v = 0; v < K; v += 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(xr + v);
+                ar[v] += sg * q.x; ar[v + 1] += sg * q.y; ar[v + 2] += sg * q.z; ar[v + 3] += sg * q.w;
+              }
+            } else {
+#pragma unroll
+              for (int v = 0; v < K; v++) ar[v] += sg * xr[v];
+            }
+          } else {
+            const float cr = (float)S.cs[2 * ph] * w, ci = (float)S.cs[2 * ph + 1] * w;
+            const float2 *xc = reinterpret_cast<const float2 *>(S.x) + j * K;
+#pragma unroll
+            for (int v = 0; v < K; v++) {
+              const float2 q = xc[v];
+              ar[v] += cr * q.x - ci * q.y;
+              ai[v] += cr * q.y + ci * q.x;
+            }
+          }
+        }
+        diag += P.jzq[c] * (float)((P.cls_off[c + 1] - P.cls_off[c]) - 2 * nanti);
+#pragma unroll
+        for (int v = 0; v < K; v++) { yr[v] += P.jh[c] * ar[v]; yi[v] += P.jh[c] * ai[v]; }
+      }
+      const float rs = (float)S.rsqrt_tab[ti];
+      if (!S.cplx) {
+        const float *xi = reinterpret_cast<const float *>(S.x) + i * K;
+        float *yo = reinterpret_cast<float *>(S.y) + i * K;
+#pragma unroll
+        for (int v = 0; v < K; v++) yo[v] = diag * xi[v] + yr[v] * rs;
+      } else {
+        const float2 *xi = reinterpret_cast<const float2 *>(S.x) + i * K;
+        float2 *yo = reinterpret_cast<float2 *>(S.y) + i * K;
+#pragma unroll
+        for (int v = 0; v < K; v++) {
+          const float2 q = xi[v];
+          yo[v] = make_float2(diag * q.x + yr[v] * rs, diag * q.y + yi[v] * rs);
+        }
+      }
+    }
+  }
+}
+
+// Work-item prefix sums for a tile, and the sector table, to the device (synchronous).
+int upload(ed_batch *Bt, int rows_per_item) {
+  std::vector<int64_t> item0(Bt->n);
+  int64_t acc = 0;
+  for (int s = 0; s < Bt->n; s++) {
+    item0[s] = acc;
+    Bt->host[s].item0 = acc;
+    acc += (Bt->host[s].D + rows_per_item - 1) / rows_per_item;
+  }
+  Bt->n_items = acc;
+  ED_CK(cudaMemcpy(Bt->d_item0, item0.data(), (size_t)Bt->n * 8, cudaMemcpyHostToDevice));
+  ED_CK(cudaMemcpy(Bt->d_sec, Bt->host.data(), sizeof(BatchSector) * Bt->n, cudaMemcpyHostToDevice));
+  return ED_OK;
+}
+
+// Counter reset and the persistent kernel (the part that is captured in the graph).
+int launch(ed_batch *Bt, int rows_per_item, cudaStream_t st) {
+  BatchParams P{};
+  P.sec = Bt->d_sec;
+  P.item0 = Bt->d_item0;
+  P.n_sec = Bt->n;
+  P.n_items = Bt->n_items;
+  P.rows_per_item = rows_per_item;
+  P.counter = Bt->d_counter;
+  P.bond = Bt->d_bond;
+  P.n_classes = Bt->n_classes;
+  for (int c = 0; c <= Bt->n_classes; c++) P.cls_off[c] = Bt->cls_off[c];
+  for (int c = 0; c < Bt->n_classes; c++) { P.jh[c] = (float)Bt->jh[c]; P.jzq[c] = (float)Bt->jzq[c]; }
+  ED_CK(cudaMemsetAsync(Bt->d_counter, 0, 8, st));
+  const int grid = Bt->sm_count * 8;
+  switch (Bt->k) {
+    case 1: batch_kernel<1><<<grid, 256, 0, st>>>(P); break;
+    case 2: batch_kernel<2><<<grid, 256, 0, st>>>(P); break;
+    case 4: batch_kernel<4><<<grid, 256, 0, st>>>(P); break;
+    case 8: batch_kernel<8><<<grid, 256, 0, st>>>(P); break;
+    default: return ed_fail(ED_ERR_INVALID, "block width k must be 1, 2, 4 or 8");
+  }
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+}  // namespace
+
+extern "C" int ed_batch_create(ed_basis *const *bases, int32_t n, const double *J, const double *Jz,
+                               int32_t k, ed_batch **out) {
+  if (!bases || n < 1 || !J || !Jz || !out) return ed_fail(ED_ERR_INVALID, "null argument");
+  if (k != 1 && k != 2 && k != 4 && k != 8) return ed_fail(ED_ERR_INVALID, "block width k must be 1, 2, 4 or 8");
+  *out = nullptr;
+  const ed_basis *b0 = bases[0];
+  if (!b0) return ed_fail(ED_ERR_INVALID, "null basis");
+  if (2 * b0->n_bonds > 2 * ED_MAXBONDS / 8) return ed_fail(ED_ERR_UNSUPPORTED, "at most 512 bonds in a batch");
+  for (int s = 1; s < n; s++) {
+    if (!bases[s]) return ed_fail(ED_ERR_INVALID, "null basis");
+    if (bases[s]->N != b0->N || bases[s]->bond_pos != b0->bond_pos || bases[s]->cls_off != b0->cls_off)
+      return ed_fail(ED_ERR_INVALID, "sectors of a batch must share sites, bonds and classes");
+  }
+  ed_batch *Bt = new (std::nothrow) ed_batch();
+  if (!Bt) return ed_fail(ED_ERR_OOM, "host allocation failed");
+  Bt->n = n;
+  Bt->k = k;
+  Bt->n_classes = b0->n_classes;
+  Bt->n_bonds = b0->n_bonds;
+  Bt->sm_count = b0->sm_count;
+  Bt->bases.assign(bases, bases + n);
+  for (int c = 0; c <= b0->n_classes; c++) Bt->cls_off[c] = b0->cls_off[c];
+  for (int c = 0; c < b0->n_classes; c++) { Bt->jh[c] = 0.5 * J[c]; Bt->jzq[c] = 0.25 * J[c] * Jz[c]; }
+  Bt->host.resize(n);
+  for (int s = 0; s < n; s++) {
+    const ed_basis *B = bases[s];
+    BatchSector &S = Bt->host[s];
+    S.T = B->T;
+    S.I = B->I;
+    S.sqrt_tab = B->d_sqrt;
+    S.rsqrt_tab = B->d_rsqrt;
+    S.cs = B->d_cs;
+    S.D = B->D;
+    S.cplx = B->is_real ? 0 : 1;
+  }
+  if (cudaMalloc(&Bt->d_sec, sizeof(BatchSector) * n) != cudaSuccess ||
+      cudaMalloc(&Bt->d_item0, 8 * (size_t)n) != cudaSuccess || cudaMalloc(&Bt->d_counter, 8) != cudaSuccess ||
+      cudaMalloc(&Bt->d_bond, std::max<size_t>(b0->bond_pos.size(), 1)) != cudaSuccess) {
+    cudaGetLastError();
+    ed_batch_free(Bt);
+    return ed_fail(ED_ERR_OOM, "cannot allocate the batch");
+  }
+  if (cudaMemcpy(Bt->d_bond, b0->bond_pos.data(), b0->bond_pos.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    ed_batch_free(Bt);
+    return ed_fail(ED_ERR_CUDA, "cannot upload bonds");
+  }
+  *out = Bt;
+  return ED_OK;
+}
+
+extern "C" int ed_batch_set_vectors(ed_batch *Bt, void *const *x, void *const *y) {
+  if (!Bt || !x || !y) return ed_fail(ED_ERR_INVALID, "null argument");
+  for (int s = 0; s < Bt->n; s++) {
+    if (Bt->host[s].D > 0 && (!x[s] || !y[s])) return ed_fail(ED_ERR_INVALID, "null vector of a non-empty sector");
+    Bt->host[s].x = x[s];
+    Bt->host[s].y = y[s];
+  }
+  Bt->vectors_set = true;
+  if (Bt->rows_per_item) {   // the kernel reads the sector table from device memory
+    ED_CK(cudaMemcpy(Bt->d_sec, Bt->host.data(), sizeof(BatchSector) * Bt->n, cudaMemcpyHostToDevice));
+  }
+  return ED_OK;
+}
+
+extern "C" int ed_batch_apply(ed_batch *Bt, void *stream) {
+  if (!Bt) return ed_fail(ED_ERR_INVALID, "null batch");
+  if (!Bt->vectors_set) return ed_fail(ED_ERR_INVALID, "ed_batch_set_vectors first");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if (!Bt->rows_per_item) {
+    // pick the tile: time each candidate (second of two runs) and keep the fastest
+    const int cand[] = {64, 256, 1024, 4096};
+    cudaEvent_t e0, e1;
+    ED_CK(cudaEventCreate(&e0));
+    ED_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int pick = 256;
+    for (int c : cand) {
+      float ms = 0;
+      if ((rc = upload(Bt, c))) return rc;
+      for (int rep = 0; rep < 2; rep++) {
+        ED_CK(cudaEventRecord(e0, st));
+        if ((rc = launch(Bt, c, st))) return rc;
+        ED_CK(cudaEventRecord(e1, st));
+        ED_CK(cudaEventSynchronize(e1));
+        ED_CK(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ms < best) { best = ms; pick = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    Bt->rows_per_item = pick;
+    if ((rc = upload(Bt, pick))) return rc;
+  }
+  if (!Bt->exec) {   // capture counter reset + launch once, replay afterwards
+    cudaStream_t cs;
+    ED_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    ED_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    rc = launch(Bt, Bt->rows_per_item, cs);
+    cudaGraph_t gg = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &gg);
+    if (rc) { if (gg) cudaGraphDestroy(gg); cudaStreamDestroy(cs); return rc; }
+    if (ce != cudaSuccess) { cudaStreamDestroy(cs); return ed_cuda_fail(ce, "cudaStreamEndCapture"); }
+    g = gg;
+    const cudaError_t ie = cudaGraphInstantiate(&Bt->exec, g, 0);
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (ie != cudaSuccess) return ed_cuda_fail(ie, "cudaGraphInstantiate");
+  }
+  ED_CK(cudaGraphLaunch(Bt->exec, st));
+  return ED_OK;
+}
+
+extern "C" int ed_batch_info(const ed_batch *Bt, int32_t *rows_per_item, int64_t *n_items) {
+  if (!Bt) return ed_fail(ED_ERR_INVALID, "null batch");
+  if (rows_per_item) *rows_per_item = Bt->rows_per_item;
+  if (n_items) *n_items = Bt->n_items;
+  return ED_OK;
+}
+
+extern "C" void ed_batch_free(ed_batch *Bt) {
+  if (!Bt) return;
+  if (Bt->exec) cudaGraphExecDestroy(Bt->exec);
+  if (Bt->d_sec) cudaFree(Bt->d_sec);
+  if (Bt->d_item0) cudaFree(Bt->d_item0);
+  if (Bt->d_counter) cudaFree(Bt->d_counter);
+  if (Bt->d_bond) cudaFree(Bt->d_bond);
+  delete Bt;
+}

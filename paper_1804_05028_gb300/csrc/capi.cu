@@ -49,7 +49,7 @@ int validate(ed_basis *B, const ed_lattice *L, const ed_group *G, const ed_irrep
   if (N % L->n_sublat) return ed_fail(ED_ERR_UNSTABLE, "n_sublat does not divide n_sites");
   const int n = N / L->n_sublat;
   if (L->n_sublat > 1 && n > 20) return ed_fail(ED_ERR_UNSUPPORTED, "sublattice blocks above 20 sites");
-  if (L->n_sublat == 1 && N > 24) return ed_fail(ED_ERR_UNSUPPORTED, "a single sublattice needs N <= 24");
+  if (L->n_sublat == 1 && N > 26) return ed_fail(ED_ERR_UNSUPPORTED, "a single sublattice needs N <= 26");
   if (L->n_bonds < 1 || L->n_bonds > ED_MAXBONDS || !L->bonds || !L->bond_class)
     return ed_fail(ED_ERR_INVALID, "bonds missing or more than 4096");
   if (L->n_classes < 1 || L->n_classes > ED_MAXCLS)
@@ -177,10 +177,79 @@ int validate(ed_basis *B, const ed_lattice *L, const ed_group *G, const ed_irrep
   return ED_OK;
 }
 
+// norm and character tables, bond positions (every split)
+int build_norm_tables(ed_basis *B, cudaStream_t st) {
+  const int ns = B->nsym;
+  auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+    if (bytes == 0) { *dst = nullptr; return ED_OK; }
+    if (cudaMalloc(dst, bytes) != cudaSuccess) { cudaGetLastError(); return ed_fail(ED_ERR_OOM, "cannot allocate lookup tables"); }
+    ED_CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st));
+    B->table_bytes += bytes;
+    return ED_OK;
+  };
+  int rc;
+  std::vector<double> sq(ns + 1), rs(ns + 1), cs(2 * (size_t)B->denom);
+  for (int t = 0; t <= ns; t++) { sq[t] = std::sqrt((double)t); rs[t] = t ? 1.0 / std::sqrt((double)t) : 0.0; }
+  for (int k = 0; k < B->denom; k++) {
+    const double a = 2.0 * M_PI * (double)k / (double)B->denom;
+    cs[2 * k] = std::cos(a);
+    cs[2 * k + 1] = std::sin(a);
+  }
+  if ((rc = up((void **)&B->d_sqrt, sq.data(), sq.size() * 8))) return rc;
+  if ((rc = up((void **)&B->d_rsqrt, rs.data(), rs.size() * 8))) return rc;
+  if ((rc = up((void **)&B->d_cs, cs.data(), cs.size() * 8))) return rc;
+  if ((rc = up((void **)&B->d_bond_pos, B->bond_pos.data(), B->bond_pos.size()))) return rc;
+  if ((rc = up((void **)&B->d_bond_pad, B->bond_pad.data(), B->bond_pad.size()))) return rc;
+  if ((rc = up((void **)&B->d_bond_blk, B->bond_blk.data(), B->bond_blk.size() * 4))) return rc;
+  ED_CK(cudaStreamSynchronize(st));
+  return ED_OK;
+}
+
+// One sublattice: the whole table (Sec. III, "store the representative and g for every
+// state"), built on the device, or shared with another basis of the same group.
+int build_full_table(ed_basis *B, cudaStream_t st, const ed_basis *share) {
+  const int N = B->N, ns = B->nsym;
+  auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+    if (cudaMalloc(dst, bytes) != cudaSuccess) { cudaGetLastError(); return ed_fail(ED_ERR_OOM, "cannot allocate lookup tables"); }
+    ED_CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st));
+    B->table_bytes += bytes;
+    return ED_OK;
+  };
+  std::vector<uint8_t> pbit((size_t)ns * N);
+  for (int g = 0; g < ns; g++)
+    for (int b = 0; b < N; b++)   // bit b is label N-1-b; its image label perm[g][N-1-b]
+      pbit[(size_t)g * N + b] = (uint8_t)(N - 1 - B->perm[(size_t)g * N + (N - 1 - b)]);
+  int rc;
+  if ((rc = up((void **)&B->d_pbit, pbit.data(), pbit.size()))) return rc;
+  if ((rc = up((void **)&B->d_phase, B->phase.data(), B->phase.size() * 4))) return rc;
+  if (share && share->full_tab && share->N == N && share->nsym == ns && share->perm == B->perm) {
+    B->full_tab = share->full_tab;
+  } else {
+    uint64_t *t = nullptr;
+    if (cudaMalloc(&t, ((size_t)1 << N) * 8) != cudaSuccess) {
+      cudaGetLastError();
+      return ed_fail(ED_ERR_OOM, "cannot allocate the one-sublattice table");
+    }
+    B->full_tab = std::shared_ptr<uint64_t>(t, [](uint64_t *q) { cudaFree(q); });
+    B->table_bytes += ((size_t)1 << N) * 8;
+    if ((rc = ed_build_full_table(B->d_pbit, N, ns, t, st))) return rc;
+  }
+  bool triv = true;
+  for (int g = 0; g < ns; g++) triv = triv && B->phase[g] == 0;
+  DevTables &T = B->T;
+  T.N = N; T.nsub = 1; T.n = N; T.nsym = ns; T.denom = B->denom;
+  T.chi_trivial = triv ? 1 : 0;
+  T.full = B->full_tab.get();
+  T.pbit = B->d_pbit;
+  T.phase = B->d_phase;
+  return build_norm_tables(B, st);
+}
+
 // Alg. 1: for every sublattice X, substate and group element, SymmetryAction_X; then
 // Rep_X = min over G_X (elements carrying X onto block 0) and Sym_X = its minimisers.
-int build_tables(ed_basis *B, cudaStream_t st) {
+int build_tables(ed_basis *B, cudaStream_t st, const ed_basis *share) {
   const int N = B->N, nsub = B->nsub, n = B->n, ns = B->nsym;
+  if (nsub == 1) return build_full_table(B, st, share);
   const size_t nn = (size_t)1 << n;
   std::vector<uint8_t> dest((size_t)ns * nsub);
   for (int g = 0; g < ns; g++)
@@ -306,34 +375,21 @@ int build_tables(ed_basis *B, cudaStream_t st) {
   T.action_u16 = u16 ? 1 : 0;
   T.rep = B->d_rep; T.sym_off = B->d_sym_off; T.sym_list = B->d_sym_list;
   T.action = B->d_action; T.dest = B->d_dest; T.phase = B->d_phase;
-  // norm and character tables
-  std::vector<double> sq(ns + 1), rs(ns + 1), cs(2 * (size_t)B->denom);
-  for (int t = 0; t <= ns; t++) { sq[t] = std::sqrt((double)t); rs[t] = t ? 1.0 / std::sqrt((double)t) : 0.0; }
-  for (int k = 0; k < B->denom; k++) {
-    const double a = 2.0 * M_PI * (double)k / (double)B->denom;
-    cs[2 * k] = std::cos(a);
-    cs[2 * k + 1] = std::sin(a);
-  }
-  if ((rc = up((void **)&B->d_sqrt, sq.data(), sq.size() * 8))) return rc;
-  if ((rc = up((void **)&B->d_rsqrt, rs.data(), rs.size() * 8))) return rc;
-  if ((rc = up((void **)&B->d_cs, cs.data(), cs.size() * 8))) return rc;
-  if ((rc = up((void **)&B->d_bond_pos, B->bond_pos.data(), B->bond_pos.size()))) return rc;
-  if ((rc = up((void **)&B->d_bond_pad, B->bond_pad.data(), B->bond_pad.size()))) return rc;
-  if ((rc = up((void **)&B->d_bond_blk, B->bond_blk.data(), B->bond_blk.size() * 4))) return rc;
-  ED_CK(cudaStreamSynchronize(st));
-  return ED_OK;
+  T.chi_trivial = 0;
+  return build_norm_tables(B, st);
 }
 
 void free_all(ed_basis *B) {
   void *ptrs[] = {B->d_rep, B->d_sym_off, B->d_sym_list, B->d_action, B->d_dest, B->d_phase,
                   B->d_src, B->d_e1, B->d_rid, B->d_e2, B->d_off2, B->d_list2, B->d_bond_pad,
-                  B->d_bond_blk,
+                  B->d_bond_blk, B->d_pbit,
                   B->d_basis, B->d_stab, B->d_top_rank, B->d_limits,
                   B->d_postfix == B->d_basis ? nullptr : B->d_postfix,
                   B->d_sqrt, B->d_rsqrt, B->d_cs, B->d_bond_pos, B->d_partial,
                   B->d_stage_x, B->d_stage_y};
   for (void *p : ptrs) if (p) cudaFree(p);
   if (B->h_partial) cudaFreeHost(B->h_partial);
+  B->full_tab.reset();
 }
 
 size_t elem_size(int dtype) {
@@ -454,7 +510,7 @@ extern "C" int ed_build_basis(const ed_lattice *L, const ed_group *G, const ed_i
   if (e != cudaSuccess) { delete B; return ed_cuda_fail(e, "cudaGetDevice"); }
   e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
   if (e != cudaSuccess) { delete B; return ed_cuda_fail(e, "cudaDeviceGetAttribute"); }
-  if ((rc = build_tables(B, st))) { free_all(B); delete B; return rc; }
+  if ((rc = build_tables(B, st, opts ? opts->share_tables : nullptr))) { free_all(B); delete B; return rc; }
   const int bucket = (opts && opts->bucket_target > 0) ? opts->bucket_target : 4;
   if ((rc = ed_build_device(B, st, bucket))) { free_all(B); delete B; return rc; }
   B->n_partial = ED_MAXCLS * B->sm_count * 8;   // per-class partials of the widest grid

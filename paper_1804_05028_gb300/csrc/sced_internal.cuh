@@ -25,6 +25,12 @@ struct DevTables {
   int N, nsub, n, nsym;
   int denom;
   int action_u16;
+  int chi_trivial;           // every character is 1 (no projection check needed)
+  // one sublattice: the whole lookup table (Sec. III, second option), per configuration
+  // rep | first minimising g << 32 | number of minimisers << 48, and the permutations as
+  // bit maps pbit[g*N + b] = bit that bit b is carried to (for the projection check)
+  const uint64_t *full;
+  const uint8_t *pbit;
   const uint32_t *rep;
   const uint32_t *sym_off;
   const uint16_t *sym_list;
@@ -74,6 +80,17 @@ __device__ __forceinline__ RepOut find_rep(const DevTables &T, const uint32_t *r
                                            const uint32_t *symoff_s, const uint16_t *symlist_s,
                                            const uint8_t *dest_s, const int32_t *phase_s,
                                            uint64_t s) {
+  if (T.full) {   // one block: the table holds the answer (a representative that the
+                  // projection removes is simply absent from Basis)
+    RepOut f;
+    if (s >> T.N) { f.rep = ~0ULL; f.g = -1; f.t = 0; f.mixed = 1; return f; }
+    const uint64_t e = __ldg(T.full + s);
+    f.rep = e & 0xFFFFFFFFull;
+    f.g = (int)((e >> 32) & 0xFFFF);
+    f.t = (int)(e >> 48);
+    f.mixed = 0;
+    return f;
+  }
   const int n = T.n, nsub = T.nsub, N = T.N;
   const uint32_t mask = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
   uint32_t sub[ED_MAXSUB], r[ED_MAXSUB];
@@ -127,6 +144,24 @@ __device__ __forceinline__ bool is_kept_rep(const DevTables &T, const uint32_t *
                                             const uint32_t *symoff_s, const uint16_t *symlist_s,
                                             const uint8_t *dest_s, const int32_t *phase_s,
                                             uint64_t s, int *t_out) {
+  if (T.full) {
+    const uint64_t e = __ldg(T.full + s);
+    if ((e & 0xFFFFFFFFull) != s) return false;
+    if (!T.chi_trivial) {   // the projection survives iff chi = 1 on the stabiliser
+      for (int g = 0; g < T.nsym; g++) {
+        if (phase_s[g] == 0) continue;
+        uint64_t v = 0, m = s;
+        while (m) {
+          const int b = __ffsll((long long)m) - 1;
+          m &= m - 1;
+          v |= 1ULL << T.pbit[g * T.N + b];
+        }
+        if (v == s) return false;
+      }
+    }
+    *t_out = (int)(e >> 48);
+    return true;
+  }
   const int n = T.n, nsub = T.nsub, N = T.N;
   const uint32_t mask = (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
   uint32_t sub[ED_MAXSUB], r[ED_MAXSUB];
@@ -214,6 +249,7 @@ __device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
 // ---------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -245,6 +281,8 @@ struct ed_basis {
   uint8_t *d_bond_pad = nullptr;
   uint32_t *d_bond_blk = nullptr;
   int32_t *d_phase = nullptr;
+  std::shared_ptr<uint64_t> full_tab;  // one-sublattice table, shareable between sectors
+  uint8_t *d_pbit = nullptr;
   size_t sym_list_len = 0;
   size_t table_bytes = 0;
   // basis + index
@@ -302,5 +340,8 @@ int ed_launch_start(const ed_basis *B, void *v, uint64_t seed, int dtype, cudaSt
 int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
                          void *y, int dtype, int64_t r0, int64_t r1, double *partial,
                          cudaStream_t st, int mode);
+int ed_build_full_table(const uint8_t *d_pbit, int N, int nsym, uint64_t *out, cudaStream_t st);
+struct ed_batch;
+extern "C" void ed_batch_free(ed_batch *batch);
 int ed_launch_count(const ed_basis *B, unsigned long long *d_out, cudaStream_t st);
 int ed_launch_copy(const ed_basis *B, void *dst, const void *src, int dtype, cudaStream_t st);

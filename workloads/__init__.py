@@ -393,12 +393,13 @@ def config_tilted40(n_sublat: int = 4) -> Problem:
                             J1=1.0, J2=0.0, n_up=20, name="tilted40_GammaA")
 
 
-def config_square25_sectors(J2: float = 0.3, n_up_max: int = 12):
-    """Every (n_up <= 12, momentum, little-group 1-D irrep) sector of the 5x5 J1-J2 torus."""
+def config_square25_sectors(J2: float = 0.3, n_up_values=range(13, 26)):
+    """Every (S^z = 1/2 .. 25/2, momentum, little-group 1-D irrep) sector of the 5x5 J1-J2
+    torus (n_up = 13 .. 25), one sublattice (no split of 25 sites is stable under C4v)."""
     out = []
     for m in momenta((5, 0), (0, 5)):
         for ir in range(n_point_irreps((5, 0), (0, 5), m)):
             p = square_torus(5, momentum=m, point_irrep=ir, n_sublat=1, J1=1.0, J2=J2, n_up=0)
-            for n_up in range(0, n_up_max + 1):
+            for n_up in n_up_values:
                 out.append(dataclasses.replace(p, n_up=n_up, name=f"sq25_k{m}_ir{ir}_up{n_up}"))
     return out
