@@ -42,7 +42,7 @@ class _Prob(ctypes.Structure):
                 ("n_classes", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("perm", ctypes.c_void_p), ("phase_num", ctypes.c_void_p),
                 ("bonds", ctypes.c_void_p), ("bond_class", ctypes.c_void_p),
-                ("J", ctypes.c_void_p), ("Jz", ctypes.c_void_p)]
+                ("J", ctypes.c_void_p), ("Jz", ctypes.c_void_p), ("flip", ctypes.c_void_p)]
 
 
 def lib():
@@ -77,10 +77,13 @@ class OracleProblem:
         self._bcls = np.ascontiguousarray(p.bond_class, dtype=np.int32)
         self._J = np.ascontiguousarray(p.J, dtype=np.float64)
         self._Jz = np.ascontiguousarray(p.Jz, dtype=np.float64)
+        fl = getattr(p, "flip", None)
+        self._flip = None if fl is None else np.ascontiguousarray(fl, dtype=np.uint8)
         self.s = _Prob(p.n_sites, p.n_sym, p.phase_denom, p.n_bonds, p.n_classes, 0,
                        self._perm.ctypes.data, self._pnum.ctypes.data,
                        self._bonds.ctypes.data, self._bcls.ctypes.data,
-                       self._J.ctypes.data, self._Jz.ctypes.data)
+                       self._J.ctypes.data, self._Jz.ctypes.data,
+                       None if self._flip is None else self._flip.ctypes.data)
 
     @property
     def ref(self):
@@ -235,20 +238,27 @@ def dimension_formula(p) -> int:
     """D_rho = (1/|G|) sum_g chi(g)^* F(g) (projection onto a 1-D irrep).
 
     F(g), the number of configurations with n_up up spins left unchanged by g,
-    is the coefficient of x^n_up in prod over cycles c of g of (1 + x^|c|).
-    Exact integer arithmetic on the phases; a closed form independent of any
-    representative search.
+    is the coefficient of x^n_up in prod over cycles c of g of (1 + x^|c|).  For
+    an element that also reverses every spin, a fixed configuration alternates
+    along every cycle, so F = 2^(number of cycles) when all cycles have even
+    length (and then n_up = N/2 automatically), else 0.  Exact integer arithmetic
+    on the phases; a closed form independent of any representative search.
     """
     N, n_up = p.n_sites, p.n_up
+    flip = getattr(p, "flip", None)
     acc = 0j
     for g in range(p.n_sym):
-        poly = np.zeros(N + 1, dtype=object)
-        poly[0] = 1
-        for L in _cycle_lengths(p.perm[g]):
-            new = poly.copy()
-            new[L:] = new[L:] + poly[:N + 1 - L]
-            poly = new
-        F = int(poly[n_up]) if 0 <= n_up <= N else 0
+        cyc = _cycle_lengths(p.perm[g])
+        if flip is not None and flip[g]:
+            F = (2 ** len(cyc)) if (all(L % 2 == 0 for L in cyc) and 2 * n_up == N) else 0
+        else:
+            poly = np.zeros(N + 1, dtype=object)
+            poly[0] = 1
+            for L in cyc:
+                new = poly.copy()
+                new[L:] = new[L:] + poly[:N + 1 - L]
+                poly = new
+            F = int(poly[n_up]) if 0 <= n_up <= N else 0
         ang = -2 * math.pi * int(p.phase_num[g]) / p.phase_denom
         acc += F * complex(math.cos(ang), math.sin(ang))
     val = acc / p.n_sym
@@ -367,6 +377,8 @@ def sublattice_tables(p, n_sublat: int, X: int, sub: int):
     """
     N = p.n_sites
     n = N // n_sublat
+    if getattr(p, "flip", None) is not None:
+        raise NotImplementedError("sublattice tables of the worked examples: no spin flip")
     blk = lambda Y: set(range(Y * n, (Y + 1) * n))
     vals = {}
     for g in range(p.n_sym):

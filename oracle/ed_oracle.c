@@ -39,16 +39,22 @@ typedef struct {
   const int32_t *bond_class;
   const double *J;         /* [n_classes] exchange (flip amplitude J/2) */
   const double *Jz;        /* [n_classes] anisotropy of the S^z S^z part */
+  const uint8_t *flip;     /* [n_sym] or NULL: element g also reverses every spin */
 } or_problem;
 
 static inline int spin(uint64_t s, int N, int p) { return (int)((s >> (N - 1 - p)) & 1ULL); }
 
-/* (g s)[perm[p]] = s[p], one site at a time */
+/* (g s)[perm[p]] = s[p], one site at a time; an element with the spin flip then
+ * reverses every spin (up <-> down) */
 static uint64_t apply_sym(const or_problem *P, int g, uint64_t s) {
   const int32_t *perm = P->perm + (size_t)g * P->N;
   uint64_t r = 0;
   for (int p = 0; p < P->N; p++)
     if (spin(s, P->N, p)) r |= 1ULL << (P->N - 1 - perm[p]);
+  if (P->flip && P->flip[g]) {
+    const uint64_t all = (P->N == 64) ? ~0ULL : ((1ULL << P->N) - 1ULL);
+    r ^= all;
+  }
   return r;
 }
 

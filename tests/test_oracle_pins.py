@@ -206,3 +206,37 @@ def test_planted_mistakes_are_caught(name, mutate):
         if np.abs(M - Hp).max() > 1e-8:
             caught = True
     assert caught, name
+
+
+# ---------------------------------------------------------------- spin flip (Z2)
+@pytest.mark.parametrize("base", [w.chain(12, 2, k=0, n_up=6), w.chain(12, 2, k=5, n_up=6),
+                                  w.chain(10, 1, k=3, n_up=5),
+                                  w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=0.5,
+                                                 n_sublat=4, n_up=8)])
+def test_spin_flip_sectors(base):
+    """Even and odd flip sectors: dimensions add up to the unflipped sector's, the
+    projection count (flip elements fix alternating configurations only) matches the
+    enumeration, and the two spectra together are the unflipped spectrum."""
+    ev_all, dims = [], []
+    for parity in (0, 1):
+        p = w.with_spin_flip(base, parity)
+        b, _ = oracle.basis(p)
+        assert b.size == oracle.dimension_formula(p)
+        dims.append(b.size)
+        if b.size:
+            H, _, _ = oracle.hamiltonian(p)
+            Hd = H.toarray()
+            assert np.abs(Hd - Hd.conj().T).max() < 1e-14
+            ev_all.extend(np.linalg.eigvalsh(Hd))
+    H0, b0, _ = oracle.hamiltonian(base)
+    assert sum(dims) == b0.size
+    assert np.abs(np.sort(ev_all) - np.linalg.eigvalsh(H0.toarray())).max() < 1e-11
+
+
+def test_spin_flip_literal_projection():
+    for parity in (0, 1):
+        p = w.with_spin_flip(w.chain(10, 2, k=3, n_up=5), parity)
+        H, bs, _ = oracle.hamiltonian(p)
+        Hp, bs2, dropped = oracle.projected_hamiltonian(p)
+        assert np.array_equal(bs, bs2) and dropped < 1e-12
+        assert np.abs(H.toarray() - Hp).max() < 1e-13

@@ -39,7 +39,7 @@ __all__ = [
     "Problem", "chain", "square_cluster", "square_torus", "tilted_square_40",
     "point_group_irreps", "momenta", "state_uniform", "state_gaussian",
     "splitmix64", "config_chain16", "config_square36", "config_square25_sectors",
-    "config_tilted40", "C4V_OPS", "C4V_NAMES", "n_point_irreps",
+    "config_tilted40", "C4V_OPS", "C4V_NAMES", "n_point_irreps", "with_spin_flip",
 ]
 
 
@@ -59,6 +59,7 @@ class Problem:
     Jz: tuple                  # per class
     coords: np.ndarray | None = None   # (N, 2) real-space coordinate of each label
     sym_names: list | None = None
+    flip: np.ndarray | None = None     # (n_sym,) uint8: element also reverses every spin
 
     @property
     def n_sym(self) -> int:
@@ -80,6 +81,30 @@ class Problem:
         J = tuple(float(v) for v in J)
         Jz = tuple(float(v) for v in (Jz if Jz is not None else self.Jz))
         return dataclasses.replace(self, J=J, Jz=Jz)
+
+
+def with_spin_flip(p: Problem, parity: int) -> Problem:
+    """The group G x Z2 of p's group and the reversal of every spin, for the S^z = 0
+    sector (n_up = N/2), in the even (parity 0) or odd (parity 1) irrep of the flip.
+
+    Element (g, f) acts as s -> g s with every spin reversed when f = 1; its character
+    is chi(g) (-1)^(f parity).  The paper uses this symmetry in all its benchmarks
+    (Sec. V, Table 1: "even" / "odd").
+    """
+    if 2 * p.n_up != p.n_sites:
+        raise ValueError("the spin flip maps the sector to itself only at n_up = N/2")
+    if getattr(p, "flip", None) is not None:
+        raise ValueError("already has the spin flip")
+    denom = math.lcm(p.phase_denom, 2)
+    base = (p.phase_num.astype(np.int64) * (denom // p.phase_denom)) % denom
+    odd = (base + (denom // 2 if parity else 0)) % denom
+    names = p.sym_names or [f"g{i}" for i in range(p.n_sym)]
+    return dataclasses.replace(
+        p, name=f"{p.name}_flip{'odd' if parity else 'even'}",
+        perm=np.concatenate([p.perm, p.perm]).astype(np.int32), phase_denom=denom,
+        phase_num=np.concatenate([base, odd]).astype(np.int32),
+        flip=np.concatenate([np.zeros(p.n_sym, np.uint8), np.ones(p.n_sym, np.uint8)]),
+        sym_names=names + [n + "*F" for n in names])
 
 
 # ----------------------------------------------------------------------------
