@@ -67,10 +67,13 @@ typedef struct {
   const int32_t *bond_class;  /* [n_bonds] in [0, n_classes) */
 } ed_lattice;
 
-/* Symmetry group as site permutations (host memory). */
+/* Symmetry group as site permutations, optionally combined with the reversal of every
+ * spin (the spin-flip symmetry of the S^z = 0 sector, Sec. V, Table 1) (host memory). */
 typedef struct {
   int32_t n_sym;              /* |G|, 1..65535 */
   const int32_t *perm;        /* [n_sym][n_sites] */
+  const uint8_t *flip;        /* NULL, or [n_sym]: 1 when element g also reverses every spin,
+                                 (g s) = perm(s) XOR (all ones); needs n_up = N/2 */
 } ed_group;
 
 /* One-dimensional irrep as exact phases (host memory). */

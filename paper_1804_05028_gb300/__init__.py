@@ -47,7 +47,7 @@ class _Lattice(ctypes.Structure):
 
 
 class _Group(ctypes.Structure):
-    _fields_ = [("n_sym", ctypes.c_int32), ("perm", ctypes.c_void_p)]
+    _fields_ = [("n_sym", ctypes.c_int32), ("perm", ctypes.c_void_p), ("flip", ctypes.c_void_p)]
 
 
 class _Irrep(ctypes.Structure):
@@ -381,7 +381,8 @@ def dot_noalloc(x, y, out, stream=None):
 
 
 def build_basis(n_sites, n_sublat, bonds, bond_class, n_classes, perm, phase_num, phase_denom,
-                n_up, J=None, Jz=None, bucket_target=None, share_tables=None, stream=None) -> Basis:
+                n_up, J=None, Jz=None, bucket_target=None, share_tables=None, flip=None,
+                stream=None) -> Basis:
     """Validate a sector, build the sublattice tables and the basis on the current device."""
     bonds = np.ascontiguousarray(bonds, dtype=np.int32)
     bcls = np.ascontiguousarray(bond_class, dtype=np.int32)
@@ -389,7 +390,8 @@ def build_basis(n_sites, n_sublat, bonds, bond_class, n_classes, perm, phase_num
     pnum = np.ascontiguousarray(phase_num, dtype=np.int32)
     L = _Lattice(int(n_sites), int(n_sublat), int(bonds.shape[0]), int(n_classes),
                  bonds.ctypes.data, bcls.ctypes.data)
-    G = _Group(int(perm.shape[0]), perm.ctypes.data)
+    flip_a = None if flip is None else np.ascontiguousarray(flip, dtype=np.uint8)
+    G = _Group(int(perm.shape[0]), perm.ctypes.data, None if flip_a is None else flip_a.ctypes.data)
     R = _Irrep(int(phase_denom), pnum.ctypes.data)
     opts = _Opts()
     opts.bucket_target = int(bucket_target or 0)
@@ -404,7 +406,8 @@ def build_basis_from(problem, **kw) -> Basis:
     """build_basis from an object with the fields of a problem descriptor."""
     p = problem
     return build_basis(p.n_sites, p.n_sublat, p.bonds, p.bond_class, p.n_classes, p.perm,
-                       p.phase_num, p.phase_denom, p.n_up, J=p.J, Jz=p.Jz, **kw)
+                       p.phase_num, p.phase_denom, p.n_up, J=p.J, Jz=p.Jz,
+                       flip=getattr(p, "flip", None), **kw)
 
 
 def build_sectors(problems, **kw):
@@ -412,7 +415,9 @@ def build_sectors(problems, **kw):
     whose lattice and group coincide (the table depends on the group only)."""
     out, first_of_group = [], {}
     for p in problems:
-        key = (p.n_sites, p.n_sublat, np.asarray(p.perm).tobytes())
+        fl = getattr(p, "flip", None)
+        key = (p.n_sites, p.n_sublat, np.asarray(p.perm).tobytes(),
+               None if fl is None else np.asarray(fl).tobytes())
         share = first_of_group.get(key) if p.n_sublat == 1 else None
         B = build_basis_from(p, share_tables=share, **kw)
         if p.n_sublat == 1 and key not in first_of_group:

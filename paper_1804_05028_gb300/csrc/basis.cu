@@ -268,11 +268,15 @@ __global__ void make_postfix(const uint64_t *basis, int64_t D, uint64_t mask, PT
 // The whole lookup table of a one-sublattice split: every configuration s < 2^N gets its
 // representative (Eq. 4, every group element applied), the first minimising element and
 // the number of minimisers.  pbit[g*N + b] is the bit that g carries bit b to.
-__global__ void full_table_kernel(const uint8_t *pbit, int N, int nsym, uint64_t *out) {
+__global__ void full_table_kernel(const uint8_t *pbit, const uint8_t *flip, int N, int nsym,
+                                  uint64_t *out) {
   extern __shared__ uint8_t sp[];
+  uint8_t *sf = sp + nsym * N;
   for (int k = threadIdx.x; k < nsym * N; k += blockDim.x) sp[k] = pbit[k];
+  for (int k = threadIdx.x; k < nsym; k += blockDim.x) sf[k] = flip ? flip[k] : 0;
   __syncthreads();
   const uint64_t total = 1ULL << N;
+  const uint64_t all = total - 1ULL;
   for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total;
        s += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t best = ~0ULL;
@@ -285,6 +289,7 @@ __global__ void full_table_kernel(const uint8_t *pbit, int N, int nsym, uint64_t
         m &= m - 1;
         v |= 1ULL << pg[b];
       }
+      if (sf[g]) v ^= all;   // the element also reverses every spin
       if (v < best) { best = v; gb = g; cnt = 1; }
       else if (v == best) cnt++;
     }
@@ -301,15 +306,16 @@ uint64_t binom_host(int n, int k) {
 
 }  // namespace
 
-int ed_build_full_table(const uint8_t *d_pbit, int N, int nsym, uint64_t *out, cudaStream_t st) {
-  const size_t sm = (size_t)nsym * N;
+int ed_build_full_table(const uint8_t *d_pbit, const uint8_t *d_flip, int N, int nsym,
+                        uint64_t *out, cudaStream_t st) {
+  const size_t sm = (size_t)nsym * N + nsym;
   if (sm > 200 * 1024) return ed_fail(ED_ERR_UNSUPPORTED, "group too large for the one-block table");
   if (sm > 48 * 1024)
     ED_CK(cudaFuncSetAttribute(full_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int dev = 0, nsm = 0;
   ED_CK(cudaGetDevice(&dev));
   ED_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  full_table_kernel<<<nsm * 8, 256, sm, st>>>(d_pbit, N, nsym, out);
+  full_table_kernel<<<nsm * 8, 256, sm, st>>>(d_pbit, d_flip, N, nsym, out);
   ED_CK(cudaGetLastError());
   return ED_OK;
 }

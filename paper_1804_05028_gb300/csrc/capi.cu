@@ -68,18 +68,25 @@ int validate(ed_basis *B, const ed_lattice *L, const ed_group *G, const ed_irrep
       if (q < 0 || q >= N || seen[q]++) return ed_fail(ED_ERR_INVALID, "permutation " + std::to_string(g) + " is not a bijection");
     }
   }
-  // closure and homomorphism: (g h)[p] = g[h[p]], phase(g h) = phase(g) + phase(h)
+  // closure and homomorphism: (g h)[p] = g[h[p]], flips add mod 2,
+  // phase(g h) = phase(g) + phase(h)
+  auto fl = [&](int g) -> int { return G->flip ? (G->flip[g] ? 1 : 0) : 0; };
+  bool any_flip = false;
+  for (int g = 0; g < ns; g++) any_flip = any_flip || fl(g);
+  if (any_flip && 2 * n_up != N)
+    return ed_fail(ED_ERR_INVALID, "the spin flip needs n_up = N/2");
   std::unordered_multimap<uint64_t, int> index;
-  for (int g = 0; g < ns; g++) index.emplace(hash_perm(G->perm + (size_t)g * N, N), g);
-  auto find = [&](const int32_t *p) -> int {
-    auto rng = index.equal_range(hash_perm(p, N));
+  for (int g = 0; g < ns; g++) index.emplace(hash_perm(G->perm + (size_t)g * N, N) ^ (uint64_t)fl(g), g);
+  auto find = [&](const int32_t *p, int f) -> int {
+    auto rng = index.equal_range(hash_perm(p, N) ^ (uint64_t)f);
     for (auto it = rng.first; it != rng.second; ++it)
-      if (!memcmp(G->perm + (size_t)it->second * N, p, sizeof(int32_t) * N)) return it->second;
+      if (fl(it->second) == f && !memcmp(G->perm + (size_t)it->second * N, p, sizeof(int32_t) * N))
+        return it->second;
     return -1;
   };
   bool has_id = false;
   for (int g = 0; g < ns && !has_id; g++) {
-    bool id = true;
+    bool id = fl(g) == 0;
     for (int p = 0; p < N && id; p++) id = G->perm[(size_t)g * N + p] == p;
     if (id) {
       has_id = true;
@@ -92,7 +99,7 @@ int validate(ed_basis *B, const ed_lattice *L, const ed_group *G, const ed_irrep
     for (int g = 0; g < ns; g++)
       for (int h = 0; h < ns; h++) {
         for (int p = 0; p < N; p++) c[p] = G->perm[(size_t)g * N + G->perm[(size_t)h * N + p]];
-        const int k = find(c.data());
+        const int k = find(c.data(), fl(g) ^ fl(h));
         if (k < 0) return ed_fail(ED_ERR_INVALID, "group is not closed");
         if (mod((int64_t)R->phase_num[g] + R->phase_num[h] - R->phase_num[k], R->phase_denom))
           return ed_fail(ED_ERR_INVALID, "characters are not a homomorphism");
@@ -134,6 +141,8 @@ int validate(ed_basis *B, const ed_lattice *L, const ed_group *G, const ed_irrep
   B->n_bonds = L->n_bonds;
   B->n_classes = L->n_classes;
   B->perm.assign(G->perm, G->perm + (size_t)ns * N);
+  B->flip.assign(ns, 0);
+  for (int g = 0; g < ns; g++) B->flip[g] = (uint8_t)fl(g);
   B->phase.resize(ns);
   bool real = true;
   for (int g = 0; g < ns; g++) {
@@ -222,7 +231,9 @@ int build_full_table(ed_basis *B, cudaStream_t st, const ed_basis *share) {
   int rc;
   if ((rc = up((void **)&B->d_pbit, pbit.data(), pbit.size()))) return rc;
   if ((rc = up((void **)&B->d_phase, B->phase.data(), B->phase.size() * 4))) return rc;
-  if (share && share->full_tab && share->N == N && share->nsym == ns && share->perm == B->perm) {
+  if ((rc = up((void **)&B->d_flip, B->flip.data(), B->flip.size()))) return rc;
+  if (share && share->full_tab && share->N == N && share->nsym == ns && share->perm == B->perm &&
+      share->flip == B->flip) {
     B->full_tab = share->full_tab;
   } else {
     uint64_t *t = nullptr;
@@ -232,7 +243,7 @@ int build_full_table(ed_basis *B, cudaStream_t st, const ed_basis *share) {
     }
     B->full_tab = std::shared_ptr<uint64_t>(t, [](uint64_t *q) { cudaFree(q); });
     B->table_bytes += ((size_t)1 << N) * 8;
-    if ((rc = ed_build_full_table(B->d_pbit, N, ns, t, st))) return rc;
+    if ((rc = ed_build_full_table(B->d_pbit, B->d_flip, N, ns, t, st))) return rc;
   }
   bool triv = true;
   for (int g = 0; g < ns; g++) triv = triv && B->phase[g] == 0;
@@ -241,6 +252,7 @@ int build_full_table(ed_basis *B, cudaStream_t st, const ed_basis *share) {
   T.chi_trivial = triv ? 1 : 0;
   T.full = B->full_tab.get();
   T.pbit = B->d_pbit;
+  T.flip = B->d_flip;
   T.phase = B->d_phase;
   return build_norm_tables(B, st);
 }
@@ -276,6 +288,7 @@ int build_tables(ed_basis *B, cudaStream_t st, const ed_basis *share) {
         uint32_t v = 0;
         for (int k = 0; k < n; k++)
           if ((sub >> (n - 1 - k)) & 1) v |= 1u << (n - 1 - posg[g][k]);
+        if (B->flip[g]) v ^= (uint32_t)(nn - 1);   // the element also reverses every spin
         val[g] = v;
         if (need_action) {
           const size_t o = ((size_t)X * nn + sub) * ns + g;
@@ -382,7 +395,7 @@ int build_tables(ed_basis *B, cudaStream_t st, const ed_basis *share) {
 void free_all(ed_basis *B) {
   void *ptrs[] = {B->d_rep, B->d_sym_off, B->d_sym_list, B->d_action, B->d_dest, B->d_phase,
                   B->d_src, B->d_e1, B->d_rid, B->d_e2, B->d_off2, B->d_list2, B->d_bond_pad,
-                  B->d_bond_blk, B->d_pbit,
+                  B->d_bond_blk, B->d_pbit, B->d_flip,
                   B->d_basis, B->d_stab, B->d_top_rank, B->d_limits,
                   B->d_postfix == B->d_basis ? nullptr : B->d_postfix,
                   B->d_sqrt, B->d_rsqrt, B->d_cs, B->d_bond_pos, B->d_partial,

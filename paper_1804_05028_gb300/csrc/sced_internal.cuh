@@ -31,6 +31,7 @@ struct DevTables {
   // bit maps pbit[g*N + b] = bit that bit b is carried to (for the projection check)
   const uint64_t *full;
   const uint8_t *pbit;
+  const uint8_t *flip;       // [nsym] spin reversal of each element (one-sublattice table)
   const uint32_t *rep;
   const uint32_t *sym_off;
   const uint16_t *sym_list;
@@ -156,6 +157,7 @@ __device__ __forceinline__ bool is_kept_rep(const DevTables &T, const uint32_t *
           m &= m - 1;
           v |= 1ULL << T.pbit[g * T.N + b];
         }
+        if (T.flip && T.flip[g]) v ^= (T.N == 64) ? ~0ULL : ((1ULL << T.N) - 1ULL);
         if (v == s) return false;
       }
     }
@@ -260,6 +262,7 @@ struct ed_basis {
   int N = 0, nsub = 1, n = 0, nsym = 0, n_up = 0, denom = 1, n_bonds = 0, n_classes = 0;
   bool is_real = true;
   std::vector<int32_t> perm, phase;
+  std::vector<uint8_t> flip;           // [nsym] spin reversal (empty: none)
   std::vector<uint8_t> bond_pos;       // [n_bonds][2] bit positions (class-sorted)
   std::vector<int32_t> cls_off;        // [n_classes+1] bond ranges per class
   std::vector<uint8_t> bond_pad;       // bonds padded per class to words of 32 (inert (0,0))
@@ -283,6 +286,7 @@ struct ed_basis {
   int32_t *d_phase = nullptr;
   std::shared_ptr<uint64_t> full_tab;  // one-sublattice table, shareable between sectors
   uint8_t *d_pbit = nullptr;
+  uint8_t *d_flip = nullptr;
   size_t sym_list_len = 0;
   size_t table_bytes = 0;
   // basis + index
@@ -340,7 +344,8 @@ int ed_launch_start(const ed_basis *B, void *v, uint64_t seed, int dtype, cudaSt
 int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
                          void *y, int dtype, int64_t r0, int64_t r1, double *partial,
                          cudaStream_t st, int mode);
-int ed_build_full_table(const uint8_t *d_pbit, int N, int nsym, uint64_t *out, cudaStream_t st);
+int ed_build_full_table(const uint8_t *d_pbit, const uint8_t *d_flip, int N, int nsym,
+                        uint64_t *out, cudaStream_t st);
 struct ed_batch;
 extern "C" void ed_batch_free(ed_batch *batch);
 int ed_launch_count(const ed_basis *B, unsigned long long *d_out, cudaStream_t st);

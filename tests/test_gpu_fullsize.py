@@ -86,3 +86,23 @@ def test_square36_j1j2_gamma_a1():
 
 def test_tilted40_gamma_a():
     _check_sector(w.config_tilted40(), 2000, 10000, 200)
+
+
+def test_square36_spin_flip_even_odd():
+    """The 6x6 Gamma-A1 S^z = 0 sector split by the spin flip: dimensions add up, both
+    halves pass the sampled checks, and the lower ground state of the two equals the
+    unflipped sector's."""
+    import paper_1804_05028_gb300 as ed
+    base = w.config_square36()
+    e, dims = [], []
+    for parity in (0, 1):
+        p = w.with_spin_flip(base, parity)
+        _check_sector(p, 1000, 5000, 100)
+        B = ed.build_basis_from(p)
+        dims.append(B.dim)
+        e.append(B.lanczos()["E0"])
+        B.close()
+    B0 = ed.build_basis_from(base)
+    assert sum(dims) == B0.dim
+    e0 = B0.lanczos()["E0"]
+    assert abs(min(e) - e0) < 1e-10 * abs(e0)

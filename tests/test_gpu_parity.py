@@ -48,6 +48,12 @@ SMALL = [
     w.square_torus(4, momentum=(1, 0), point_irrep=1, J2=0.5, n_sublat=4, n_up=8),
     w.square_torus(4, momentum=(1, 1), point_irrep=0, J2=0.5, n_sublat=1, n_up=6),
     w.square_torus(3, momentum=(1, 2), point_irrep=0, J2=0.4, n_sublat=1, n_up=4),
+    # spin flip (Z2) at S^z = 0
+    w.with_spin_flip(w.chain(12, 2, k=0, n_up=6), 0),
+    w.with_spin_flip(w.chain(12, 1, k=5, n_up=6), 1),
+    w.with_spin_flip(w.chain(16, 4, k=3, n_up=8), 1),
+    w.with_spin_flip(w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=0.5, n_sublat=4, n_up=8), 0),
+    w.with_spin_flip(w.square_torus(4, momentum=(2, 2), point_irrep=1, J2=0.5, n_sublat=2, n_up=8), 1),
 ]
 
 
@@ -196,6 +202,8 @@ def test_couplings_and_anisotropy():
     w.config_chain16(),
     w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=0.5, n_sublat=4, n_up=8),
     w.chain(16, 2, k=5, n_up=8),
+    w.with_spin_flip(w.config_chain16(), 0),
+    w.with_spin_flip(w.config_chain16(), 1),
 ], ids=_id)
 def test_lanczos_E0(p):
     B = gpu_basis(p)
