@@ -22,6 +22,7 @@
 // (two-float) accumulator, fp64 in fp64.  Each y_i written once; no atomics.
 #include "sced_internal.cuh"
 #include <algorithm>
+#include <type_traits>
 
 namespace {
 
@@ -48,6 +49,7 @@ struct TwoParams {
   const void *postfix;
   int r_bits, q_bits, post_bits, post_bytes;
   int L;                         // bits below the top block: (NSUB - 1) n <= 32
+  int id_g;                      // index of the identity element
   uint32_t qmask, pmask;
   int64_t D;
   const void *x;
@@ -79,9 +81,31 @@ __device__ __forceinline__ void cp(unsigned char *sm, uint32_t off, const T *g, 
   for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) d[k] = g[k];
 }
 
-// g s restricted to block X: an n-bit value on block dest(g, X) (SymmetryAction_X, Eq. 11)
+// g s restricted to block X: an n-bit value on block dest(g, X) (SymmetryAction_X, Eq. 11).
+// The identity leaves every block in place, so its lookups are skipped: level 1 meets it
+// whenever the minimal block is already its own Rep (often, as the exchanged state
+// differs from a representative in two sites), level 2 whenever the images are already
+// minimal for K_R.
+// The table (|G| 2^n entries per sublattice, about 1 MB for 4 x 2^9 x 144) is read at
+// random by every thread: the load asks L1 to keep its lines over the streamed data.
 __device__ __forceinline__ uint32_t act(const TwoParams &P, int X, uint32_t sub, int g) {
-  return __ldg(P.act + (((uint32_t)X << P.n) | sub) * (uint32_t)P.nsym + (uint32_t)g);
+  if (g == P.id_g) return sub;
+  const unsigned short *a = P.act + (((uint32_t)X << P.n) | sub) * (uint32_t)P.nsym + (uint32_t)g;
+  unsigned short r;
+  asm volatile("ld.global.nc.L1::evict_last.u16 %0, [%1];" : "=h"(r) : "l"(a));
+  return r;
+}
+
+// x_j of a found representative: a gather with no reuse to speak of, kept out of L1.
+template <typename V>
+__device__ __forceinline__ V gather_x(const V *x, int64_t j) {
+  if constexpr (std::is_same<V, float>::value) {
+    float f;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(f) : "l"(x + j));
+    return f;
+  } else {
+    return x[j];
+  }
 }
 
 __device__ __forceinline__ void consider(Rep2 &o, uint32_t low, int ph) {
@@ -240,10 +264,14 @@ __device__ __forceinline__ int64_t lookup_two(const Sm2 &S, const TwoParams &P, 
   return -1;
 }
 
+// Resident 512-thread blocks per SM for the kernel without level-2 tables: three
+// (40 registers a thread) hide more of the dependent table loads than two (64).
+constexpr int kMinBlocks = 3;
+
 // kMode 0: y = H x (and optional <x, y> partials); kMode 1: per coupling class the
 // partial sums of Re <x | H_c x> with unit exchange, into partial[c * grid + block].
 template <typename V, int NSUB, bool kE2, int kMode>
-__global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : 2) apply_two_kernel(const TwoParams P) {
+__global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : kMinBlocks) apply_two_kernel(const TwoParams P) {
   using A = typename Vf<V>::A;
   constexpr bool kC = Vf<V>::cplx;
   constexpr bool kF32 = sizeof(A) == 4;
@@ -294,7 +322,7 @@ __global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : 2) apply_two_kerne
           if (R.mixed) continue;
           const int64_t j = lookup_two(S, P, R.minrep, R.low);
           if (j < 0) continue;
-          const V xj = x[j];
+          const V xj = gather_x(x, j);
           const int t = R.t, ph = R.ph;
           if constexpr (!kC) {
             if constexpr (kF32) {
@@ -420,6 +448,7 @@ int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, T
   P.r_bits = B->I.r_bits; P.q_bits = B->I.q_bits; P.post_bits = B->I.post_bits;
   P.post_bytes = B->I.post_bytes; P.D = B->D;
   P.L = (B->nsub - 1) * B->n;
+  P.id_g = B->id_g;
   P.qmask = P.q_bits >= 32 ? 0xFFFFFFFFu : ((1u << P.q_bits) - 1u);
   P.pmask = P.post_bits >= 32 ? 0xFFFFFFFFu : ((1u << P.post_bits) - 1u);
   P.bond_blk = B->d_bond_blk;
@@ -491,7 +520,7 @@ int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, c
   if (rc) return rc;
   P.x = x; P.y = y; P.r0 = r0; P.r1 = r1; P.partial = partial;
   const int bs = e2 ? 1024 : 512;
-  int grid = B->sm_count * (e2 ? 1 : 2);
+  int grid = B->sm_count * (e2 ? 1 : kMinBlocks);
   const int64_t need = (r1 - r0 + bs - 1) / bs;
   if (need < grid) grid = (int)need;
   if (grid < 1) grid = 1;

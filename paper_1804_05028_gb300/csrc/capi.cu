@@ -90,6 +90,7 @@ int validate(ed_basis *B, const ed_lattice *L, const ed_group *G, const ed_irrep
     for (int p = 0; p < N && id; p++) id = G->perm[(size_t)g * N + p] == p;
     if (id) {
       has_id = true;
+      B->id_g = g;
       if (mod(R->phase_num[g], R->phase_denom)) return ed_fail(ED_ERR_INVALID, "chi(identity) != 1");
     }
   }

@@ -263,6 +263,7 @@ struct ed_basis {
   bool is_real = true;
   std::vector<int32_t> perm, phase;
   std::vector<uint8_t> flip;           // [nsym] spin reversal (empty: none)
+  int id_g = 0;                        // index of the identity element
   std::vector<uint8_t> bond_pos;       // [n_bonds][2] bit positions (class-sorted)
   std::vector<int32_t> cls_off;        // [n_classes+1] bond ranges per class
   std::vector<uint8_t> bond_pad;       // bonds padded per class to words of 32 (inert (0,0))
