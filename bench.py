@@ -56,14 +56,16 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, dtype: str):
-    """DRAM bytes per apply_h launch from the committed ncu summary, if the kernel source
-    has not changed since it was taken (else None)."""
+def profiled(workload: str, key: str, dtype: str):
+    """A per-launch counter of the product kernel from the committed ncu summary
+    (`traffic_bytes_per_launch`: dram__bytes_read.sum + dram__bytes_write.sum;
+    `warp_instructions_per_launch`: smsp__inst_executed.sum), if the kernel source has
+    not changed since it was taken (else None)."""
     path = os.path.join(ROOT, "profiles", f"apply_h_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m = re.search(rf"traffic_bytes_per_launch\[{dtype}\]:\s*([0-9]+)\s+source_sha:\s*([0-9a-f]+)", txt)
+    m = re.search(rf"{key}\[{dtype}\]:\s*([0-9]+)\s+source_sha:\s*([0-9a-f]+)", txt)
     if not m or m.group(2) != kernel_hash():
         return None
     return int(m.group(1))
@@ -135,6 +137,12 @@ def alg_bytes(D: int, n_off: int, vec_bytes: int) -> int:
     """Bytes the method must move per product: per row the state (8), |Stab| (2), x_i and
     y_i; per off-diagonal term one gathered x_j."""
     return D * (8 + 2 + 2 * vec_bytes) + n_off * vec_bytes
+
+
+def sector_bytes(D: int, n_off: int, vec_bytes: int) -> int:
+    """As alg_bytes, but each random x_j gather costs the whole 32-byte DRAM sector it
+    sits in (the bound if no gathered x_j ever hit in L2)."""
+    return D * (8 + 2 + 2 * vec_bytes) + n_off * 32
 
 
 def cpu_baseline(p, states, seconds: float, seed: int = 7):
@@ -320,6 +328,7 @@ def main():
         del psi32
 
     pk, pk_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     results = {}
     for name, dt, vb in (("f64", torch.float64, 8), ("mixed", torch.float32, 4)):
         work = torch.empty(3 * D, dtype=dt, device="cuda")
@@ -336,13 +345,26 @@ def main():
         apply_ms = r["ms_apply"] / args.steps
         ab = alg_bytes(D, n_off, vb)
         achieved = ab / (apply_ms * 1e-3) / 1e9
+        clk = cs.summary()
+        # instruction-issue roof: every SM issues at most one warp instruction per cycle on
+        # each of its 4 schedulers, at the SM clock sampled during the timed region
+        winst = profiled(args.workload, "warp_instructions_per_launch", name)
+        issue_peak = 4 * n_sm * clk["sm_mhz"] * 1e6 / 1e9 if clk.get("sm_mhz") else None
+        issue = None
+        if winst is not None and issue_peak:
+            ia = winst / (apply_ms * 1e-3) / 1e9
+            issue = {"bound": "issue", "achieved": ia, "peak": issue_peak, "unit": "Gwarp-inst/s",
+                     "frac": ia / issue_peak, "warp_instructions_per_launch": winst,
+                     "peak_kind": "4 x SMs x sampled SM clock"}
         results[name] = {
             "value": world * nnz * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
-            "apply_ms": apply_ms, "clocks": cs.summary(),
+            "apply_ms": apply_ms, "clocks": clk,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
-                         "traffic": profiled_traffic(args.workload, name),
-                         "alg_bytes_per_launch": ab},
+                         "traffic": profiled(args.workload, "traffic_bytes_per_launch", name),
+                         "alg_bytes_per_launch": ab,
+                         "sector_bytes_per_launch": sector_bytes(D, n_off, vb)},
+            "roofline_issue": issue,
             "gpu_launches": 3 * args.steps + 2,
         }
         del work
@@ -392,7 +414,8 @@ def main():
                        "l2": "inputs larger than L2: basis %d MB, each vector %d MB" % (D * 8 >> 20, D * (4 if head_name == 'mixed' else 8) >> 20),
                        "index": {k: info[k] for k in ("prefix_rank_bits", "prefix_raw_bits", "postfix_bits", "n_keys", "max_bucket")},
                        "parallelism": f"replicas x{world}"},
-            "roofline": head["roofline"], "clocks": head["clocks"], "gpu_launches": head["gpu_launches"],
+            "roofline": head["roofline"], "roofline_issue": head["roofline_issue"],
+            "clocks": head["clocks"], "gpu_launches": head["gpu_launches"],
             "e2e": e2e, "cpu_baseline": cpu, "headline": head_name,
             "fp64": results["f64"], "mixed": results["mixed"], "accuracy": acc, "batch": batch,
             "kernel_sha": kernel_hash(),

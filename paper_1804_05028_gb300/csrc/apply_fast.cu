@@ -103,6 +103,10 @@ __device__ __forceinline__ V gather_x(const V *x, int64_t j) {
     float f;
     asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(f) : "l"(x + j));
     return f;
+  } else if constexpr (std::is_same<V, double>::value) {
+    double f;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(f) : "l"(x + j));
+    return f;
   } else {
     return x[j];
   }
@@ -290,8 +294,10 @@ __global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : kMinBlocks) apply_
   for (int c = 0; c < (kMode == 1 ? ED_MAXCLS : 1); c++) cls_dot[c] = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = P.r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.r1; i += stride) {
-    const uint64_t s = __ldg(P.basis + i);
-    const int ti = __ldg(P.stab + i);
+    // the row's own state, stabiliser order and y_i are touched once: streamed (evict
+    // first) so that they do not push the gathered x out of L2
+    const uint64_t s = __ldcs(reinterpret_cast<const unsigned long long *>(P.basis) + i);
+    const int ti = __ldcs(P.stab + i);
     uint32_t sub[NSUB];
 #pragma unroll
     for (int X = 0; X < NSUB; X++) sub[X] = (uint32_t)(s >> (N - (X + 1) * n)) & bmask;
@@ -368,7 +374,7 @@ __global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : kMinBlocks) apply_
     if constexpr (!kC) {
       const double xi = (double)x[i];
       const A yi = (A)(diag * xi + row_re * rs);
-      y[i - P.r0] = yi;
+      __stcs(y + (i - P.r0), yi);
       if (P.partial) dot_re += xi * (double)yi;
     } else {
       const V xv = x[i];
