@@ -44,9 +44,12 @@ WORKLOADS = {
                  "C4 (160), Gamma-A", workloads.config_tilted40),
     "chain16": ("Heisenberg chain N=16 periodic, Sz=0, C16, k=0", workloads.config_chain16),
 }
+# the product kernels and the code that lays out the tables and the index they read
 KERNEL_SOURCES = ["paper_1804_05028_gb300/csrc/apply.cu",
                   "paper_1804_05028_gb300/csrc/apply_fast.cu",
-                  "paper_1804_05028_gb300/csrc/sced_internal.cuh"]
+                  "paper_1804_05028_gb300/csrc/sced_internal.cuh",
+                  "paper_1804_05028_gb300/csrc/basis.cu",
+                  "paper_1804_05028_gb300/csrc/capi.cu"]
 
 
 def kernel_hash() -> str:

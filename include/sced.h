@@ -86,7 +86,7 @@ typedef struct ed_basis ed_basis;   /* opaque; owns (or shares) every device tab
 
 /* Tuning of the basis and its index; pass NULL for defaults. */
 typedef struct {
-  int32_t bucket_target;      /* average states per Limits bucket (default 4) */
+  int32_t bucket_target;      /* average states per Limits bucket (default 1) */
   int32_t reserved0;
   const ed_basis *share_tables; /* optional: a basis of the same lattice and group whose
                                    one-sublattice table (n_sublat == 1) is reused instead of

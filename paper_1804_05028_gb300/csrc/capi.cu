@@ -525,7 +525,7 @@ extern "C" int ed_build_basis(const ed_lattice *L, const ed_group *G, const ed_i
   e = cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device);
   if (e != cudaSuccess) { delete B; return ed_cuda_fail(e, "cudaDeviceGetAttribute"); }
   if ((rc = build_tables(B, st, opts ? opts->share_tables : nullptr))) { free_all(B); delete B; return rc; }
-  const int bucket = (opts && opts->bucket_target > 0) ? opts->bucket_target : 4;
+  const int bucket = (opts && opts->bucket_target > 0) ? opts->bucket_target : 1;
   if ((rc = ed_build_device(B, st, bucket))) { free_all(B); delete B; return rc; }
   B->n_partial = ED_MAXCLS * B->sm_count * 8;   // per-class partials of the widest grid
   if (cudaMalloc(&B->d_partial, (size_t)B->n_partial * 8) != cudaSuccess ||
