@@ -186,12 +186,18 @@ def bench_batch(ed, torch, steps: int):
     torch.cuda.synchronize()
     build_s = time.time() - t0
     nnz = 0
+    per = []   # (D, off-diagonal terms, bytes per vector entry) of each non-empty sector
     for B in bases:
         if B.dim:
-            nnz += B.dim + B.count_terms()[1]
+            t = B.count_terms()[1]
+            nnz += B.dim + t
+            per.append((B.dim, t, 4 if B.is_real else 8))
+    pk, pk_kind = peaks()
     out = {"workload": "square25 J1-J2 (J2=0.3), 572 sectors, one launch", "sectors": len(bases),
            "dim_total": int(sum(B.dim for B in bases)), "nonzeros_per_product": nnz,
-           "build_s": build_s}
+           "build_s": build_s,
+           "l2": "inputs larger than L2: 6 whole-lattice tables of 268 MB each, basis %d MB"
+                 % (sum(d for d, _, _ in per) * 8 >> 20)}
     g = torch.Generator(device="cuda").manual_seed(1804)
     for k in (1, 4, 8):
         xs = [torch.randn(B.dim * k, dtype=torch.float32 if B.is_real else torch.complex64,
@@ -210,8 +216,14 @@ def bench_batch(ed, torch, steps: int):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        # per row: state, |Stab|, k entries of x_i and y_i; per term: k gathered entries
+        ab = sum(d * (8 + 2 + 2 * k * b) + t * k * b for d, t, b in per)
+        ach = ab / (ms * 1e-3) / 1e9
         out[f"k{k}"] = {"ms_per_apply": ms, "value": nnz * k / (ms * 1e-3),
-                        "unit": "nonzero-vector products/s", **bt.info()}
+                        "unit": "nonzero-vector products/s", **bt.info(),
+                        "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                     "frac": ach / pk["hbm_gbs"], "peak_kind": pk_kind,
+                                     "alg_bytes_per_launch": ab}}
         bt.close()
     for B in bases:
         B.close()

@@ -280,7 +280,9 @@ int ed_batch_create(ed_basis *const *bases, int32_t n, const double *J, const do
                     int32_t k, ed_batch **out);
 
 /* ed_batch_set_vectors -- DEVICE input / output vectors per sector (HOST arrays of n device
- * pointers; x[s], y[s] hold dim_s * k elements of fp32 or complex fp32).  Synchronous. */
+ * pointers; x[s], y[s] hold dim_s * k elements of fp32 or complex fp32).  For k >= 2 every
+ * non-empty sector's x[s] and y[s] must be 16-byte aligned (the kernel moves a row's k
+ * entries with 16-byte loads and stores); ED_ERR_INVALID otherwise.  Synchronous. */
 int ed_batch_set_vectors(ed_batch *batch, void *const *x, void *const *y);
 
 /* ed_batch_apply -- y[s] = H_s x[s] for every sector, in one launch on stream.  The first call

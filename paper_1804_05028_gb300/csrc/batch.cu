@@ -14,13 +14,16 @@
 #include "sced_internal.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <vector>
 
 struct BatchSector {
   DevTables T;
   DevIndex I;
-  const double *sqrt_tab, *rsqrt_tab, *cs;
+  // fp32 copies of sqrt(t), 1/sqrt(t) and (cos, sin)(2 pi k / denom): converting the fp64
+  // tables term by term would run on the FP64 pipe
+  const float *sqrt_f, *rsqrt_f, *cs_f;
   const void *x;
   void *y;
   int64_t D;
@@ -37,6 +40,8 @@ struct ed_batch {
   int64_t *d_item0 = nullptr;
   unsigned long long *d_counter = nullptr;
   uint8_t *d_bond = nullptr;
+  float *d_ftab = nullptr;   // the sectors' fp32 norm and phase tables, back to back
+  bool all_full = false;     // every sector has a one-sublattice (whole) table
   int cls_off[ED_MAXCLS + 1];
   double jh[ED_MAXCLS], jzq[ED_MAXCLS];
   int rows_per_item = 0;   // chosen tile
@@ -71,8 +76,11 @@ __device__ __forceinline__ int sector_of(const BatchParams &P, int64_t item) {
   return lo;
 }
 
-template <int K>
-__global__ void __launch_bounds__(256) batch_kernel(const BatchParams P) {
+// kFull: every sector looks its representatives up in a whole table (one sublattice), so
+// the block-wise search is not compiled in and the kernel needs far fewer registers.
+template <int K, bool kFull>
+__global__ void __launch_bounds__(256, kFull ? (K <= 4 ? 6 : 4) : 1)
+    batch_kernel(const BatchParams P) {
   __shared__ BatchSector S;
   __shared__ int64_t item_s;
   __shared__ uint8_t bond_s[2 * ED_MAXBONDS / 8];
@@ -96,21 +104,27 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchParams P) {
       for (int v = 0; v < K; v++) { yr[v] = 0.f; yi[v] = 0.f; }
       float diag = 0.f;
       for (int c = 0; c < P.n_classes; c++) {
-        float ar[K], ai[K];
-#pragma unroll
-        for (int v = 0; v < K; v++) { ar[v] = 0.f; ai[v] = 0.f; }
+        const float jh = P.jh[c];   // the class's J/2 goes into every term's weight
         int nanti = 0;
         for (int b = P.cls_off[c]; b < P.cls_off[c + 1]; b++) {
           const int pa = bond_s[2 * b], pb = bond_s[2 * b + 1];
           if ((((s >> pa) ^ (s >> pb)) & 1ULL) == 0) continue;
           nanti++;
-          const RepOut R = find_rep(S.T, S.T.rep, S.T.sym_off, S.T.sym_list, S.T.dest, S.T.phase,
-                                    s ^ ((1ULL << pa) | (1ULL << pb)));
-          if (R.mixed) continue;
+          const uint64_t s2 = s ^ ((1ULL << pa) | (1ULL << pb));
+          RepOut R;
+          if constexpr (kFull) {
+            const uint64_t e = __ldg(S.T.full + s2);
+            R.rep = e & 0xFFFFFFFFull;
+            R.g = (int)((e >> 32) & 0xFFFF);
+            R.t = (int)(e >> 48);
+          } else {
+            R = find_rep(S.T, S.T.rep, S.T.sym_off, S.T.sym_list, S.T.dest, S.T.phase, s2);
+            if (R.mixed) continue;
+          }
           const int64_t j = lookup_index(S.I, R.rep);
           if (j < 0) continue;
-          const float w = (float)S.sqrt_tab[R.t];
-          const int ph = S.T.phase[R.g];
+          const float w = jh * __ldg(S.sqrt_f + R.t);
+          const int ph = __ldg(S.T.phase + R.g);
           if (!S.cplx) {
             const float sg = ph == 0 ? w : -w;
             const float *xr = reinterpret_cast<const float *>(S.x) + j * K;
@@ -118,40 +132,63 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchParams P) {
 #pragma unroll
               for (int v = 0; v < K; v += 4) {
                 const float4 q = *reinterpret_cast<const float4 *>(xr + v);
-                ar[v] += sg * q.x; ar[v + 1] += sg * q.y; ar[v + 2] += sg * q.z; ar[v + 3] += sg * q.w;
+                yr[v] += sg * q.x; yr[v + 1] += sg * q.y; yr[v + 2] += sg * q.z; yr[v + 3] += sg * q.w;
               }
             } else {
 #pragma unroll
-              for (int v = 0; v < K; v++) ar[v] += sg * xr[v];
+              for (int v = 0; v < K; v++) yr[v] += sg * xr[v];
             }
           } else {
-            const float cr = (float)S.cs[2 * ph] * w, ci = (float)S.cs[2 * ph + 1] * w;
+            const float cr = __ldg(S.cs_f + 2 * ph) * w, ci = __ldg(S.cs_f + 2 * ph + 1) * w;
             const float2 *xc = reinterpret_cast<const float2 *>(S.x) + j * K;
+            if constexpr (K % 2 == 0) {   // two complex entries per 16-byte load
 #pragma unroll
-            for (int v = 0; v < K; v++) {
-              const float2 q = xc[v];
-              ar[v] += cr * q.x - ci * q.y;
-              ai[v] += cr * q.y + ci * q.x;
+              for (int v = 0; v < K; v += 2) {
+                const float4 q = *reinterpret_cast<const float4 *>(xc + v);
+                yr[v] += cr * q.x - ci * q.y;
+                yi[v] += cr * q.y + ci * q.x;
+                yr[v + 1] += cr * q.z - ci * q.w;
+                yi[v + 1] += cr * q.w + ci * q.z;
+              }
+            } else {
+              const float2 q = xc[0];
+              yr[0] += cr * q.x - ci * q.y;
+              yi[0] += cr * q.y + ci * q.x;
             }
           }
         }
         diag += P.jzq[c] * (float)((P.cls_off[c + 1] - P.cls_off[c]) - 2 * nanti);
-#pragma unroll
-        for (int v = 0; v < K; v++) { yr[v] += P.jh[c] * ar[v]; yi[v] += P.jh[c] * ai[v]; }
       }
-      const float rs = (float)S.rsqrt_tab[ti];
+      const float rs = __ldg(S.rsqrt_f + ti);
       if (!S.cplx) {
         const float *xi = reinterpret_cast<const float *>(S.x) + i * K;
         float *yo = reinterpret_cast<float *>(S.y) + i * K;
+        if constexpr (K % 4 == 0) {
 #pragma unroll
-        for (int v = 0; v < K; v++) yo[v] = diag * xi[v] + yr[v] * rs;
+          for (int v = 0; v < K; v += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(xi + v);
+            *reinterpret_cast<float4 *>(yo + v) =
+                make_float4(diag * q.x + yr[v] * rs, diag * q.y + yr[v + 1] * rs,
+                            diag * q.z + yr[v + 2] * rs, diag * q.w + yr[v + 3] * rs);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < K; v++) yo[v] = diag * xi[v] + yr[v] * rs;
+        }
       } else {
         const float2 *xi = reinterpret_cast<const float2 *>(S.x) + i * K;
         float2 *yo = reinterpret_cast<float2 *>(S.y) + i * K;
+        if constexpr (K % 2 == 0) {
 #pragma unroll
-        for (int v = 0; v < K; v++) {
-          const float2 q = xi[v];
-          yo[v] = make_float2(diag * q.x + yr[v] * rs, diag * q.y + yi[v] * rs);
+          for (int v = 0; v < K; v += 2) {
+            const float4 q = *reinterpret_cast<const float4 *>(xi + v);
+            *reinterpret_cast<float4 *>(yo + v) =
+                make_float4(diag * q.x + yr[v] * rs, diag * q.y + yi[v] * rs,
+                            diag * q.z + yr[v + 1] * rs, diag * q.w + yi[v + 1] * rs);
+          }
+        } else {
+          const float2 q = xi[0];
+          yo[0] = make_float2(diag * q.x + yr[0] * rs, diag * q.y + yi[0] * rs);
         }
       }
     }
@@ -188,11 +225,15 @@ int launch(ed_batch *Bt, int rows_per_item, cudaStream_t st) {
   for (int c = 0; c < Bt->n_classes; c++) { P.jh[c] = (float)Bt->jh[c]; P.jzq[c] = (float)Bt->jzq[c]; }
   ED_CK(cudaMemsetAsync(Bt->d_counter, 0, 8, st));
   const int grid = Bt->sm_count * 8;
-  switch (Bt->k) {
-    case 1: batch_kernel<1><<<grid, 256, 0, st>>>(P); break;
-    case 2: batch_kernel<2><<<grid, 256, 0, st>>>(P); break;
-    case 4: batch_kernel<4><<<grid, 256, 0, st>>>(P); break;
-    case 8: batch_kernel<8><<<grid, 256, 0, st>>>(P); break;
+  switch (Bt->k * 2 + (Bt->all_full ? 1 : 0)) {
+#define BCASE(K)                                                     \
+  case 2 * K: batch_kernel<K, false><<<grid, 256, 0, st>>>(P); break; \
+  case 2 * K + 1: batch_kernel<K, true><<<grid, 256, 0, st>>>(P); break;
+    BCASE(1)
+    BCASE(2)
+    BCASE(4)
+    BCASE(8)
+#undef BCASE
     default: return ed_fail(ED_ERR_INVALID, "block width k must be 1, 2, 4 or 8");
   }
   ED_CK(cudaGetLastError());
@@ -225,27 +266,45 @@ extern "C" int ed_batch_create(ed_basis *const *bases, int32_t n, const double *
   for (int c = 0; c <= b0->n_classes; c++) Bt->cls_off[c] = b0->cls_off[c];
   for (int c = 0; c < b0->n_classes; c++) { Bt->jh[c] = 0.5 * J[c]; Bt->jzq[c] = 0.25 * J[c] * Jz[c]; }
   Bt->host.resize(n);
+  std::vector<float> ftab;
+  std::vector<size_t> foff(n);
+  Bt->all_full = true;
   for (int s = 0; s < n; s++) {
     const ed_basis *B = bases[s];
     BatchSector &S = Bt->host[s];
     S.T = B->T;
     S.I = B->I;
-    S.sqrt_tab = B->d_sqrt;
-    S.rsqrt_tab = B->d_rsqrt;
-    S.cs = B->d_cs;
     S.D = B->D;
     S.cplx = B->is_real ? 0 : 1;
+    if (!B->T.full) Bt->all_full = false;
+    foff[s] = ftab.size();   // sqrt [nsym+1], rsqrt [nsym+1], cs [2 denom]
+    for (int t = 0; t <= B->nsym; t++) ftab.push_back((float)std::sqrt((double)t));
+    for (int t = 0; t <= B->nsym; t++) ftab.push_back(t ? (float)(1.0 / std::sqrt((double)t)) : 0.f);
+    for (int q = 0; q < B->denom; q++) {
+      const double a = 2.0 * M_PI * (double)q / (double)B->denom;
+      ftab.push_back((float)std::cos(a));
+      ftab.push_back((float)std::sin(a));
+    }
   }
   if (cudaMalloc(&Bt->d_sec, sizeof(BatchSector) * n) != cudaSuccess ||
       cudaMalloc(&Bt->d_item0, 8 * (size_t)n) != cudaSuccess || cudaMalloc(&Bt->d_counter, 8) != cudaSuccess ||
-      cudaMalloc(&Bt->d_bond, std::max<size_t>(b0->bond_pos.size(), 1)) != cudaSuccess) {
+      cudaMalloc(&Bt->d_bond, std::max<size_t>(b0->bond_pos.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&Bt->d_ftab, ftab.size() * 4) != cudaSuccess) {
     cudaGetLastError();
     ed_batch_free(Bt);
     return ed_fail(ED_ERR_OOM, "cannot allocate the batch");
   }
-  if (cudaMemcpy(Bt->d_bond, b0->bond_pos.data(), b0->bond_pos.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemcpy(Bt->d_bond, b0->bond_pos.data(), b0->bond_pos.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(Bt->d_ftab, ftab.data(), ftab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
     ed_batch_free(Bt);
-    return ed_fail(ED_ERR_CUDA, "cannot upload bonds");
+    return ed_fail(ED_ERR_CUDA, "cannot upload bonds and tables");
+  }
+  for (int s = 0; s < n; s++) {
+    BatchSector &S = Bt->host[s];
+    const int ns = bases[s]->nsym;
+    S.sqrt_f = Bt->d_ftab + foff[s];
+    S.rsqrt_f = S.sqrt_f + ns + 1;
+    S.cs_f = S.rsqrt_f + ns + 1;
   }
   *out = Bt;
   return ED_OK;
@@ -255,6 +314,8 @@ extern "C" int ed_batch_set_vectors(ed_batch *Bt, void *const *x, void *const *y
   if (!Bt || !x || !y) return ed_fail(ED_ERR_INVALID, "null argument");
   for (int s = 0; s < Bt->n; s++) {
     if (Bt->host[s].D > 0 && (!x[s] || !y[s])) return ed_fail(ED_ERR_INVALID, "null vector of a non-empty sector");
+    if (Bt->host[s].D > 0 && Bt->k >= 2 && (((uintptr_t)x[s] | (uintptr_t)y[s]) & 15u))
+      return ed_fail(ED_ERR_INVALID, "vectors must be 16-byte aligned for k >= 2");
     Bt->host[s].x = x[s];
     Bt->host[s].y = y[s];
   }
@@ -329,5 +390,6 @@ extern "C" void ed_batch_free(ed_batch *Bt) {
   if (Bt->d_item0) cudaFree(Bt->d_item0);
   if (Bt->d_counter) cudaFree(Bt->d_counter);
   if (Bt->d_bond) cudaFree(Bt->d_bond);
+  if (Bt->d_ftab) cudaFree(Bt->d_ftab);
   delete Bt;
 }

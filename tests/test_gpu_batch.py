@@ -92,3 +92,19 @@ def test_batched_matches_single_sector(sectors, k):
                 err = (Y[:, v] - ref).abs().max().item()
                 assert err <= 2e-6 * max(ref.abs().max().item(), 1.0), (p.name, v, err)
     assert bt.info()["rows_per_item"] in (64, 256, 1024, 4096)
+
+
+def test_misaligned_vectors_rejected(sectors):
+    """k >= 2 moves a row's k entries with 16-byte accesses: a vector view that starts 4
+    bytes into its allocation is refused on the host, before any launch."""
+    import paper_1804_05028_gb300 as ed
+    probs, bases = sectors
+    sub = [B for B in bases if B.dim][:3]
+    xs = [torch.zeros(B.dim * 4 + 1, dtype=torch.float32 if B.is_real else torch.complex64,
+                      device="cuda") for B in sub]
+    ys = [torch.zeros_like(x) for x in xs]
+    bt = ed.Batch(sub, k=4)
+    with pytest.raises(ed.EdError, match="16-byte aligned"):
+        bt.set_vectors([x[1:] for x in xs], [y[1:] for y in ys])
+    bt.set_vectors([x[:-1] for x in xs], [y[:-1] for y in ys])   # aligned views pass
+    bt.close()
