@@ -267,8 +267,8 @@ int ed_expect_classes(ed_basis *basis, const double *Jz, const void *x, int32_t 
  * Batched product over many sectors (the uneven-sector workload): sectors of one lattice
  * (same sites, bonds, classes) that differ in group, irrep and n_up, each applied to k
  * vectors at once, all in one persistent launch.  Work items (sector, block of rows) are
- * taken from a device counter (atomicAdd; no CTA waits on another), so sectors of any size
- * mix in one launch.  Each exchange term is searched (Alg. 2) and looked up (Sec. IV) once
+ * taken warp by warp from a device counter (atomicAdd; no warp waits on another), so
+ * sectors of any size mix in one launch.  Each exchange term is searched (Alg. 2) and looked up (Sec. IV) once
  * and applied to the k vectors, stored row-major: x[s][i*k + v].  Vectors are fp32 for real
  * sectors and complex fp32 (interleaved) for sectors with complex characters.
  */

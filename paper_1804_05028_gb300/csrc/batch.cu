@@ -2,9 +2,9 @@
 //
 // A batch holds sectors of one lattice (same sites, bonds and couplings) that differ in
 // symmetry group, irrep and n_up, and so in dimension (from 0 to ~2e5 on the 5x5 torus).
-// One persistent launch covers all of them: every CTA takes work items -- (sector,
+// One persistent launch covers all of them: every warp takes work items -- (sector,
 // block of consecutive rows) -- from a device counter with atomicAdd until none are
-// left, so uneven sectors balance themselves and no CTA waits on another.  Each row's
+// left, so uneven sectors balance themselves and no warp waits on another.  Each row's
 // exchange terms go through the representative search and the Limits lookup once and
 // are applied to k vectors stored row-major ([D][k], so the k values of a gathered row
 // are contiguous), amortising the search over the block.  Vectors are fp32 for real
@@ -76,29 +76,42 @@ __device__ __forceinline__ int sector_of(const BatchParams &P, int64_t item) {
   return lo;
 }
 
+constexpr int kBatchThreads = 256;
+static_assert(sizeof(BatchSector) % 4 == 0, "sector descriptors are copied as 32-bit words");
+
 // kFull: every sector looks its representatives up in a whole table (one sublattice), so
 // the block-wise search is not compiled in and the kernel needs far fewer registers.
 template <int K, bool kFull>
-__global__ void __launch_bounds__(256, kFull ? (K <= 4 ? 6 : 4) : 1)
+__global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 4) : 1)
     batch_kernel(const BatchParams P) {
-  __shared__ BatchSector S;
-  __shared__ int64_t item_s;
+  // each warp takes its own work items and keeps its own copy of the sector descriptor,
+  // so no warp waits at a block-wide barrier for another warp's rows
+  __shared__ BatchSector S_w[kBatchThreads / 32];
   __shared__ uint8_t bond_s[2 * ED_MAXBONDS / 8];
   const int nb = P.cls_off[P.n_classes];
   for (int q = threadIdx.x; q < 2 * nb; q += blockDim.x) bond_s[q] = P.bond[q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  BatchSector &S = S_w[threadIdx.x >> 5];
+  int cur = -1;
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) item_s = (int64_t)atomicAdd(P.counter, 1ULL);
-    __syncthreads();
-    const int64_t item = item_s;
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(P.counter, 1ULL);
+    const int64_t item = (int64_t)__shfl_sync(0xFFFFFFFFu, it, 0);
     if (item >= P.n_items) break;
     const int sid = sector_of(P, item);
-    if (threadIdx.x == 0) S = P.sec[sid];
-    __syncthreads();
-    for (int64_t i = (item - S.item0) * P.rows_per_item + threadIdx.x;
-         i < S.D && i < (item - S.item0 + 1) * P.rows_per_item; i += blockDim.x) {
-      const uint64_t s = __ldg(S.I.basis + i);
-      const int ti = __ldg(S.I.stab + i);
+    if (sid != cur) {
+      __syncwarp();
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(P.sec + sid);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(&S);
+      for (int q = lane; q < (int)(sizeof(BatchSector) / 4); q += 32) dst[q] = __ldg(src + q);
+      __syncwarp();
+      cur = sid;
+    }
+    for (int64_t i = (item - S.item0) * P.rows_per_item + lane;
+         i < S.D && i < (item - S.item0 + 1) * P.rows_per_item; i += 32) {
+      const uint64_t s = __ldcs(reinterpret_cast<const unsigned long long *>(S.I.basis) + i);
+      const int ti = __ldcs(S.I.stab + i);
       float yr[K], yi[K];
 #pragma unroll
       for (int v = 0; v < K; v++) { yr[v] = 0.f; yi[v] = 0.f; }
@@ -227,8 +240,8 @@ int launch(ed_batch *Bt, int rows_per_item, cudaStream_t st) {
   const int grid = Bt->sm_count * 8;
   switch (Bt->k * 2 + (Bt->all_full ? 1 : 0)) {
 #define BCASE(K)                                                     \
-  case 2 * K: batch_kernel<K, false><<<grid, 256, 0, st>>>(P); break; \
-  case 2 * K + 1: batch_kernel<K, true><<<grid, 256, 0, st>>>(P); break;
+  case 2 * K: batch_kernel<K, false><<<grid, kBatchThreads, 0, st>>>(P); break; \
+  case 2 * K + 1: batch_kernel<K, true><<<grid, kBatchThreads, 0, st>>>(P); break;
     BCASE(1)
     BCASE(2)
     BCASE(4)
@@ -333,7 +346,7 @@ extern "C" int ed_batch_apply(ed_batch *Bt, void *stream) {
   int rc;
   if (!Bt->rows_per_item) {
     // pick the tile: time each candidate (second of two runs) and keep the fastest
-    const int cand[] = {64, 256, 1024, 4096};
+    const int cand[] = {32, 64, 128, 256};   // rows per work item of one warp
     cudaEvent_t e0, e1;
     ED_CK(cudaEventCreate(&e0));
     ED_CK(cudaEventCreate(&e1));
