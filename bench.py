@@ -13,7 +13,7 @@ Metric: symmetrised H x nonzeros per second = (D diagonal terms + off-diagonal t
 whose target survives the projection) per product x products per second, summed over
 ranks (each rank runs its own replica of the sector; weak scaling).
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--batch-only]
        (N > 1: launched by torch.distributed.run, one rank per GPU)
 """
 from __future__ import annotations
@@ -290,9 +290,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="time only the batched 5x5 sectors and print their JSON object")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_only:
+        import torch
+        import paper_1804_05028_gb300 as ed
+        ed.build()
+        print(json.dumps({"batch": bench_batch(ed, torch, max(args.steps, 5))}))
+        return 0
 
     import torch
     import paper_1804_05028_gb300 as ed

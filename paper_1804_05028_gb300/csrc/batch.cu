@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 4) : 1)
           }
           const int64_t j = lookup_index(S.I, R.rep);
           if (j < 0) continue;
-          const float w = jh * __ldg(S.sqrt_f + R.t);
+          float w = jh;
+          if (R.t != 1) w *= __ldg(S.sqrt_f + R.t);   // t = |Stab| of the target, mostly 1
           const int ph = __ldg(S.T.phase + R.g);
           if (!S.cplx) {
             const float sg = ph == 0 ? w : -w;
