@@ -326,10 +326,12 @@ extern "C" int ed_batch_create(ed_basis *const *bases, int32_t n, const double *
 
 extern "C" int ed_batch_set_vectors(ed_batch *Bt, void *const *x, void *const *y) {
   if (!Bt || !x || !y) return ed_fail(ED_ERR_INVALID, "null argument");
-  for (int s = 0; s < Bt->n; s++) {
+  for (int s = 0; s < Bt->n; s++) {   // check every sector before changing any
     if (Bt->host[s].D > 0 && (!x[s] || !y[s])) return ed_fail(ED_ERR_INVALID, "null vector of a non-empty sector");
     if (Bt->host[s].D > 0 && Bt->k >= 2 && (((uintptr_t)x[s] | (uintptr_t)y[s]) & 15u))
       return ed_fail(ED_ERR_INVALID, "vectors must be 16-byte aligned for k >= 2");
+  }
+  for (int s = 0; s < Bt->n; s++) {
     Bt->host[s].x = x[s];
     Bt->host[s].y = y[s];
   }
