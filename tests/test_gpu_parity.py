@@ -197,6 +197,34 @@ def test_couplings_and_anisotropy():
         assert np.abs(y - H @ x).max() < 1e-12 * np.abs(H @ x).max()
 
 
+@pytest.mark.parametrize("p", [
+    w.chain(20, 4, k=0, n_up=10),      # two-level kernel, 4 blocks of 5 sites
+    w.chain(20, 2, k=3, n_up=9),       # two-level kernel, complex characters
+    w.chain(20, 5, k=0, n_up=10),      # 5 blocks: the generic kernel (Alg. 2 as printed)
+], ids=_id)
+def test_apply_H_many_blocks_ragged_tail(p):
+    """About 9,000 rows: many 512-row thread blocks and a partial last one, the whole
+    product and row ranges that cut blocks, in fp64 and fp32."""
+    B = gpu_basis(p)
+    H, bs, _ = oracle.hamiltonian(p)
+    D = B.dim
+    assert D == bs.size and D > 8 * 512 and D % 512
+    cplx = not p.is_real()
+    x = _x_for(bs, cplx)
+    y_ref = H @ x
+    scale = np.abs(y_ref).max()
+    dt, dt32 = (torch.complex128, torch.complex64) if cplx else (torch.float64, torch.float32)
+    xt = torch.from_numpy(x).to(dt).cuda()
+    assert np.abs(B.apply_H(xt).cpu().numpy() - y_ref).max() <= 1e-12 * scale
+    cuts = [0, 1, 511, 513, D // 3, D - 7, D]
+    parts = [B.apply_H_rows(xt, a, b).cpu().numpy() for a, b in zip(cuts[:-1], cuts[1:])]
+    assert np.abs(np.concatenate(parts) - y_ref).max() <= 1e-12 * scale
+    x32 = x.astype(np.complex64 if cplx else np.float32)
+    y32 = B.apply_H(torch.from_numpy(x32).cuda()).cpu().numpy()
+    y_ref32 = H @ x32.astype(np.complex128 if cplx else np.float64)
+    assert np.abs(y32 - y_ref32).max() <= 2e-6 * scale
+
+
 # ------------------------------------------------------------------ Lanczos
 @pytest.mark.parametrize("p", [
     w.config_chain16(),
