@@ -281,8 +281,9 @@ int ed_batch_create(ed_basis *const *bases, int32_t n, const double *J, const do
 
 /* ed_batch_set_vectors -- DEVICE input / output vectors per sector (HOST arrays of n device
  * pointers; x[s], y[s] hold dim_s * k elements of fp32 or complex fp32).  For k >= 2 every
- * non-empty sector's x[s] and y[s] must be 16-byte aligned (the kernel moves a row's k
- * entries with 16-byte loads and stores); ED_ERR_INVALID otherwise.  Synchronous. */
+ * non-empty sector's x[s] and y[s] must be 16-byte aligned, and x[s] 32-byte aligned when
+ * a row holds 32 bytes or more (k = 8 real, k >= 4 complex): the kernel moves a row's k
+ * entries with 16- and 32-byte accesses.  ED_ERR_INVALID otherwise.  Synchronous. */
 int ed_batch_set_vectors(ed_batch *batch, void *const *x, void *const *y);
 
 /* ed_batch_apply -- y[s] = H_s x[s] for every sector, in one launch on stream.  The first call

@@ -77,6 +77,18 @@ __device__ __forceinline__ int sector_of(const BatchParams &P, int64_t item) {
 }
 
 constexpr int kBatchThreads = 256;
+
+// Eight fp32 values (32 bytes, 32-byte aligned) in one 256-bit load: a gathered row of
+// k >= 8 real or k >= 4 complex entries then costs one L1 request per lane, not two.
+struct F8 { float v[8]; };
+__device__ __forceinline__ F8 ld8(const float *p) {
+  F8 r;
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]),
+                 "=f"(r.v[5]), "=f"(r.v[6]), "=f"(r.v[7])
+               : "l"(p));
+  return r;
+}
 static_assert(sizeof(BatchSector) % 4 == 0, "sector descriptors are copied as 32-bit words");
 
 // kFull: every sector looks its representatives up in a whole table (one sublattice), so
@@ -142,7 +154,14 @@ __global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 4) : 1)
           if (!S.cplx) {
             const float sg = ph == 0 ? w : -w;
             const float *xr = reinterpret_cast<const float *>(S.x) + j * K;
-            if constexpr (K % 4 == 0) {
+            if constexpr (K % 8 == 0) {
+#pragma unroll
+              for (int v = 0; v < K; v += 8) {
+                const F8 q = ld8(xr + v);
+#pragma unroll
+                for (int u = 0; u < 8; u++) yr[v + u] += sg * q.v[u];
+              }
+            } else if constexpr (K % 4 == 0) {
 #pragma unroll
               for (int v = 0; v < K; v += 4) {
                 const float4 q = *reinterpret_cast<const float4 *>(xr + v);
@@ -155,7 +174,17 @@ __global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 4) : 1)
           } else {
             const float cr = __ldg(S.cs_f + 2 * ph) * w, ci = __ldg(S.cs_f + 2 * ph + 1) * w;
             const float2 *xc = reinterpret_cast<const float2 *>(S.x) + j * K;
-            if constexpr (K % 2 == 0) {   // two complex entries per 16-byte load
+            if constexpr (K % 4 == 0) {   // four complex entries per 32-byte load
+#pragma unroll
+              for (int v = 0; v < K; v += 4) {
+                const F8 q = ld8(reinterpret_cast<const float *>(xc + v));
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                  yr[v + u] += cr * q.v[2 * u] - ci * q.v[2 * u + 1];
+                  yi[v + u] += cr * q.v[2 * u + 1] + ci * q.v[2 * u];
+                }
+              }
+            } else if constexpr (K % 2 == 0) {   // two complex entries per 16-byte load
 #pragma unroll
               for (int v = 0; v < K; v += 2) {
                 const float4 q = *reinterpret_cast<const float4 *>(xc + v);
@@ -330,6 +359,9 @@ extern "C" int ed_batch_set_vectors(ed_batch *Bt, void *const *x, void *const *y
     if (Bt->host[s].D > 0 && (!x[s] || !y[s])) return ed_fail(ED_ERR_INVALID, "null vector of a non-empty sector");
     if (Bt->host[s].D > 0 && Bt->k >= 2 && (((uintptr_t)x[s] | (uintptr_t)y[s]) & 15u))
       return ed_fail(ED_ERR_INVALID, "vectors must be 16-byte aligned for k >= 2");
+    const int row_bytes = Bt->k * (Bt->host[s].cplx ? 8 : 4);
+    if (Bt->host[s].D > 0 && row_bytes >= 32 && ((uintptr_t)x[s] & 31u))
+      return ed_fail(ED_ERR_INVALID, "x must be 32-byte aligned when a row holds 32 bytes or more");
   }
   for (int s = 0; s < Bt->n; s++) {
     Bt->host[s].x = x[s];

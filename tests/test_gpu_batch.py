@@ -108,3 +108,13 @@ def test_misaligned_vectors_rejected(sectors):
         bt.set_vectors([x[1:] for x in xs], [y[1:] for y in ys])
     bt.set_vectors([x[:-1] for x in xs], [y[:-1] for y in ys])   # aligned views pass
     bt.close()
+    # k = 8: a gathered row is 32 or 64 bytes, read with 32-byte loads, so x must be
+    # 32-byte aligned; a view 16 bytes in passes the 16-byte check and not this one
+    x8 = [torch.zeros(B.dim * 8 + 4, dtype=torch.float32 if B.is_real else torch.complex64,
+                      device="cuda") for B in sub]
+    y8 = [torch.zeros(B.dim * 8, dtype=x.dtype, device="cuda") for x, B in zip(x8, sub)]
+    bt = ed.Batch(sub, k=8)
+    with pytest.raises(ed.EdError, match="32-byte aligned"):
+        bt.set_vectors([x[(4 if B.is_real else 2):][:B.dim * 8] for x, B in zip(x8, sub)], y8)
+    bt.set_vectors([x[:B.dim * 8] for x, B in zip(x8, sub)], y8)
+    bt.close()
