@@ -93,8 +93,10 @@ static_assert(sizeof(BatchSector) % 4 == 0, "sector descriptors are copied as 32
 
 // kFull: every sector looks its representatives up in a whole table (one sublattice), so
 // the block-wise search is not compiled in and the kernel needs far fewer registers.
+// Resident blocks per SM: 6 up to k = 4; 5 for k = 8 (51 registers, a 16-byte spill),
+// which beat 4 (63 registers) by 5% and 6 (42 registers) by 3%.
 template <int K, bool kFull>
-__global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 4) : 1)
+__global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 5) : 1)
     batch_kernel(const BatchParams P) {
   // each warp takes its own work items and keeps its own copy of the sector descriptor,
   // so no warp waits at a block-wide barrier for another warp's rows
