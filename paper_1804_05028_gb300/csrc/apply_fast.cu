@@ -268,14 +268,18 @@ __device__ __forceinline__ int64_t lookup_two(const Sm2 &S, const TwoParams &P, 
   return -1;
 }
 
-// Resident 512-thread blocks per SM for the kernel without level-2 tables: three
-// (40 registers a thread) hide more of the dependent table loads than two (64).
-constexpr int kMinBlocks = 3;
+// Kernel without level-2 tables in shared memory: two 768-thread blocks per SM, i.e. 48
+// warps at 40 registers.  48 warps hide more of the dependent table loads than 32 at 64
+// registers; and two blocks stage the shared tables twice where three 512-thread blocks
+// stage them three times, which leaves L1 more room for the SymmetryAction and level-2
+// lines (3-4% faster; six 256-thread blocks were 29% slower).
+constexpr int kThreads = 768;
+constexpr int kMinBlocks = 2;
 
 // kMode 0: y = H x (and optional <x, y> partials); kMode 1: per coupling class the
 // partial sums of Re <x | H_c x> with unit exchange, into partial[c * grid + block].
 template <typename V, int NSUB, bool kE2, int kMode>
-__global__ void __launch_bounds__(kE2 ? 1024 : 512, kE2 ? 1 : kMinBlocks) apply_two_kernel(const TwoParams P) {
+__global__ void __launch_bounds__(kE2 ? 1024 : kThreads, kE2 ? 1 : kMinBlocks) apply_two_kernel(const TwoParams P) {
   using A = typename Vf<V>::A;
   constexpr bool kC = Vf<V>::cplx;
   constexpr bool kF32 = sizeof(A) == 4;
@@ -485,8 +489,8 @@ int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, T
   return ED_OK;
 }
 
-// e2 staged: one 1024-thread CTA per SM (the tables take most of shared memory);
-// otherwise two 512-thread CTAs per SM.  Both give 32 warps per SM at 64 registers.
+// e2 staged: one 1024-thread CTA per SM (the tables take most of shared memory), 32
+// warps at 64 registers; otherwise two 768-thread CTAs per SM, 48 warps at 40 registers.
 template <typename V, int NSUB, int kMode = 0>
 int launch_t(const TwoParams &P, bool e2, int grid, cudaStream_t st) {
   if (e2) {
@@ -496,7 +500,7 @@ int launch_t(const TwoParams &P, bool e2, int grid, cudaStream_t st) {
   } else {
     auto k = apply_two_kernel<V, NSUB, false, kMode>;
     ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
-    k<<<grid, 512, P.smem_bytes, st>>>(P);
+    k<<<grid, kThreads, P.smem_bytes, st>>>(P);
   }
   ED_CK(cudaGetLastError());
   return ED_OK;
@@ -525,7 +529,7 @@ int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, c
   if (rc == ED_ERR_UNSUPPORTED) { e2 = false; rc = make_params(B, J, Jz, false, P); }
   if (rc) return rc;
   P.x = x; P.y = y; P.r0 = r0; P.r1 = r1; P.partial = partial;
-  const int bs = e2 ? 1024 : 512;
+  const int bs = e2 ? 1024 : kThreads;
   int grid = B->sm_count * (e2 ? 1 : kMinBlocks);
   const int64_t need = (r1 - r0 + bs - 1) / bs;
   if (need < grid) grid = (int)need;
