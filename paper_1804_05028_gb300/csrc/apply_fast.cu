@@ -64,7 +64,8 @@ struct TwoParams {
 struct Sm2 {
   const uint32_t *e2;    // level-2 tables (shared-memory copy), when staged
   const uint32_t *bblk;
-  const uint32_t *e1, *top;
+  const uint32_t *e1;
+  const uint16_t *top;   // prefix rank (< 4096), 0xFFFF where no representative has that top
   const uint8_t *rid, *dest, *src, *bond;
   const int32_t *phase;
 };
@@ -227,7 +228,13 @@ __device__ __forceinline__ Sm2 stage_two(const TwoParams &P, unsigned char *sm, 
   cp(sm, P.off_phase, P.phase, (uint32_t)P.nsym);
   cp(sm, P.off_bond, P.bond_pos, P.n_bond);
   cp(sm, P.off_bblk, P.bond_blk, P.n_bond / 2);
-  cp(sm, P.off_top, P.top_rank, P.n_top);
+  {   // the prefix rank staged as 16 bits: ranks are below 2^12
+    uint16_t *d = reinterpret_cast<uint16_t *>(sm + P.off_top);
+    for (uint32_t k = threadIdx.x; k < P.n_top; k += blockDim.x) {
+      const uint32_t v = P.top_rank[k];
+      d[k] = v == ED_NO_RANK ? (uint16_t)0xFFFFu : (uint16_t)v;
+    }
+  }
   cp(sm, P.off_sq, P.sqrt_tab, P.n_sq);
   cp(sm, P.off_sq + 8 * P.n_sq, P.rsqrt_tab, P.n_sq);
   if (cplx) cp(sm, P.off_cs, P.cs, P.n_cs);
@@ -242,7 +249,7 @@ __device__ __forceinline__ Sm2 stage_two(const TwoParams &P, unsigned char *sm, 
   S.src = sm + P.off_src;
   S.phase = reinterpret_cast<const int32_t *>(sm + P.off_phase);
   S.bond = sm + P.off_bond;
-  S.top = reinterpret_cast<const uint32_t *>(sm + P.off_top);
+  S.top = reinterpret_cast<const uint16_t *>(sm + P.off_top);
   return S;
 }
 
@@ -254,7 +261,7 @@ __device__ __forceinline__ int64_t lookup_two(const Sm2 &S, const TwoParams &P, 
                                               uint32_t low) {
   const uint64_t r = ((uint64_t)minrep << P.L) | low;
   const uint32_t rk = S.top[(uint32_t)(r >> (P.N - P.r_bits))];
-  if (rk == ED_NO_RANK) return -1;
+  if (rk == 0xFFFFu) return -1;
   const uint32_t key = (rk << P.q_bits) | ((uint32_t)(r >> P.post_bits) & P.qmask);
   uint32_t lo = __ldg(P.limits + key), hi = __ldg(P.limits + key + 1);
   const uint32_t tg = (uint32_t)r & P.pmask;
@@ -476,7 +483,7 @@ int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, T
   put(P.off_sq, 16 * (size_t)P.n_sq);
   put(P.off_cs, 8 * (size_t)P.n_cs);
   put(P.off_e1, 4 * (size_t)P.n_e1);
-  put(P.off_top, 4 * (size_t)P.n_top);
+  put(P.off_top, 2 * (size_t)P.n_top);
   put(P.off_phase, 4 * (size_t)P.nsym);
   put(P.off_e2, 4 * (size_t)P.n_e2);
   put(P.off_bblk, 2 * (size_t)P.n_bond);
@@ -500,6 +507,12 @@ int launch_t(const TwoParams &P, bool e2, int grid, cudaStream_t st) {
   } else {
     auto k = apply_two_kernel<V, NSUB, false, kMode>;
     ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
+    // ask for just the shared memory of kMinBlocks resident blocks (plus the per-block
+    // reserve); the rest of the SM's 256 KB stays L1 for the SymmetryAction and level-2
+    // lines (about 1% faster than the default split)
+    const int need = kMinBlocks * ((int)P.smem_bytes + 1536);
+    const int pct = std::min(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
+    ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
     k<<<grid, kThreads, P.smem_bytes, st>>>(P);
   }
   ED_CK(cudaGetLastError());
