@@ -436,6 +436,7 @@ def main():
                        "step": "one Lanczos iteration (apply_H with fused <v,Hv>, update with ||w||, scale)",
                        "l2": "inputs larger than L2: basis %d MB, each vector %d MB" % (D * 8 >> 20, D * (4 if head_name == 'mixed' else 8) >> 20),
                        "index": {k: info[k] for k in ("prefix_rank_bits", "prefix_raw_bits", "postfix_bits", "n_keys", "max_bucket")},
+                       "basis_build_ms": info["build_ms"],
                        "parallelism": f"replicas x{world}"},
             "roofline": head["roofline"], "roofline_issue": head["roofline_issue"],
             "clocks": head["clocks"], "gpu_launches": head["gpu_launches"],
