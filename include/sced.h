@@ -183,8 +183,11 @@ int ed_apply_H_rows(const ed_basis *basis, const double *J, const double *Jz, co
 
 /*
  * ed_apply_H_host -- ed_apply_H on HOST arrays x, y (dim elements of dtype): copies x
- * to device staging buffers owned by the basis, runs the product, copies y back.
- * Synchronous.  Not safe to call concurrently on the same basis.
+ * to device staging buffers owned by the basis, runs the product, copies y back.  Above
+ * 2^25 rows the product runs in up to 8 row chunks and each chunk of y is copied back
+ * (on a stream of the basis) while the next one is computed; with pinned host arrays
+ * the copies then overlap the product.  Synchronous.  Not safe to call concurrently on
+ * the same basis.
  */
 int ed_apply_H_host(ed_basis *basis, const double *J, const double *Jz, const void *x_host,
                     void *y_host, int32_t dtype, void *stream);

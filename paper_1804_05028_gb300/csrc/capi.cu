@@ -404,6 +404,10 @@ void free_all(ed_basis *B) {
   for (void *p : ptrs) if (p) cudaFree(p);
   if (B->h_partial) cudaFreeHost(B->h_partial);
   B->full_tab.reset();
+  for (cudaEvent_t e : B->chunk_done) cudaEventDestroy(e);
+  B->chunk_done.clear();
+  if (B->copy_stream) cudaStreamDestroy(B->copy_stream);
+  B->copy_stream = nullptr;
 }
 
 size_t elem_size(int dtype) {
@@ -627,9 +631,35 @@ extern "C" int ed_apply_H_host(ed_basis *B, const double *J, const double *Jz, c
     }
     B->stage_bytes = bytes;
   }
+  // The product needs the whole of x, so the host-to-device copy comes first.  y goes
+  // back in row chunks: the copy of chunk c (on a second stream) runs while chunk c+1
+  // is computed, so only the last chunk's copy is exposed.
+  const int64_t kMinChunkRows = (int64_t)1 << 24;   // ~64 rows per thread: chunk tails stay small
+  const int n_chunks = (int)std::min<int64_t>(8, std::max<int64_t>(1, B->D / kMinChunkRows));
+  if (n_chunks > 1 && !B->copy_stream) {
+    ED_CK(cudaStreamCreateWithFlags(&B->copy_stream, cudaStreamNonBlocking));
+  }
+  while ((int)B->chunk_done.size() < n_chunks) {
+    cudaEvent_t e;
+    ED_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    B->chunk_done.push_back(e);
+  }
+  const size_t es = elem_size(dtype);
   ED_CK(cudaMemcpyAsync(B->d_stage_x, xh, bytes, cudaMemcpyHostToDevice, st));
-  if ((rc = ed_launch_apply(B, J, Jz, B->d_stage_x, B->d_stage_y, dtype, 0, B->D, nullptr, st))) return rc;
-  ED_CK(cudaMemcpyAsync(yh, B->d_stage_y, bytes, cudaMemcpyDeviceToHost, st));
+  for (int c = 0; c < n_chunks; c++) {
+    const int64_t r0 = B->D * c / n_chunks, r1 = B->D * (c + 1) / n_chunks;
+    char *yd = (char *)B->d_stage_y + (size_t)r0 * es;
+    if ((rc = ed_launch_apply(B, J, Jz, B->d_stage_x, yd, dtype, r0, r1, nullptr, st))) return rc;
+    if (n_chunks == 1) {
+      ED_CK(cudaMemcpyAsync(yh, B->d_stage_y, bytes, cudaMemcpyDeviceToHost, st));
+    } else {
+      ED_CK(cudaEventRecord(B->chunk_done[c], st));
+      ED_CK(cudaStreamWaitEvent(B->copy_stream, B->chunk_done[c], 0));
+      ED_CK(cudaMemcpyAsync((char *)yh + (size_t)r0 * es, yd, (size_t)(r1 - r0) * es,
+                            cudaMemcpyDeviceToHost, B->copy_stream));
+    }
+  }
+  if (n_chunks > 1) ED_CK(cudaStreamSynchronize(B->copy_stream));
   ED_CK(cudaStreamSynchronize(st));
   return ED_OK;
 }

@@ -310,6 +310,8 @@ struct ed_basis {
   double *h_partial = nullptr;   // pinned
   void *d_stage_x = nullptr, *d_stage_y = nullptr;
   size_t stage_bytes = 0;
+  cudaStream_t copy_stream = nullptr;   // device-to-host copies of ed_apply_H_host
+  std::vector<cudaEvent_t> chunk_done;  // one per row chunk of ed_apply_H_host
   double build_ms = 0;
 };
 

@@ -67,6 +67,12 @@ def _check_sector(p, n_basis_samples, n_config_samples, n_rows):
     # H x on sampled rows, fp64 and fp32
     x = w.state_uniform(s, 1804)
     y = B.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
+    # the host-buffer entry point runs the product in row chunks with the copies of y
+    # overlapped; rows are independent, so it must agree bit for bit
+    xp = torch.from_numpy(x).pin_memory()
+    yp = torch.empty_like(xp).pin_memory()
+    B.apply_H_host(xp, yp)
+    assert np.array_equal(yp.numpy(), y)
     rows = np.sort(rng.choice(D, n_rows, replace=False))
     y_ref = oracle.rows(p, s[rows], lambda q: w.state_uniform(q, 1804))
     scale = np.abs(y_ref).max()
