@@ -179,17 +179,41 @@ def test_rows_equal_matrix_rows():
 
 
 # ---------------------------------------------------------------- planted mistakes
-def _mutant_matrix(p, mutate):
+def _mutant_matrix(p, mutate, mutate_diag=None, drop_last=False):
     bs, stab = oracle.basis(p)
     diag, nt, reps, val = oracle.columns(p, bs)
     D = bs.size
     M = np.zeros((D, D), complex)
-    M[np.arange(D), np.arange(D)] = diag
+    M[np.arange(D), np.arange(D)] = diag if mutate_diag is None else mutate_diag(diag)
     for i in range(D):
-        for k in range(nt[i]):
+        for k in range(nt[i] - (1 if drop_last and nt[i] else 0)):
             j = int(np.searchsorted(bs, reps[i, k]))
             M[j, i] += mutate(val[i, k], stab[i], stab[j])
     return M
+
+
+def _differs_from_projection(M_of):
+    for p in [w.chain(10, 2, k=3, n_up=5), w.chain(10, 2, k=0, n_up=5)]:
+        Hp, _, _ = oracle.projected_hamiltonian(p)
+        if np.abs(M_of(p) - Hp).max() > 1e-8:
+            return True
+    return False
+
+
+def test_unmutated_columns_equal_projection():
+    """The columns as the oracle emits them reproduce the literal Eq. 2 projection (the
+    baseline against which the planted mistakes below are detected)."""
+    assert not _differs_from_projection(lambda p: _mutant_matrix(p, lambda v, ti, tj: v))
+
+
+@pytest.mark.parametrize("name,mutate_diag,drop_last", [
+    ("S^z S^z sign", lambda d: -d, False),
+    ("S^z S^z as J/2 instead of J/4", lambda d: 2 * d, False),
+    ("one exchange term dropped per column", None, True),
+])
+def test_planted_diagonal_and_dropped_terms_are_caught(name, mutate_diag, drop_last):
+    assert _differs_from_projection(
+        lambda p: _mutant_matrix(p, lambda v, ti, tj: v, mutate_diag, drop_last)), name
 
 
 @pytest.mark.parametrize("name,mutate", [
