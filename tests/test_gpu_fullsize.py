@@ -112,3 +112,40 @@ def test_square36_spin_flip_even_odd():
     assert sum(dims) == B0.dim
     e0 = B0.lanczos()["E0"]
     assert abs(min(e) - e0) < 1e-10 * abs(e0)
+
+
+@pytest.mark.parametrize("p", [
+    w.square_torus(6, momentum=(0, 0), point_irrep=0, n_sublat=4, J1=1.0, J2=0.5, n_up=5),
+    w.square_torus(6, momentum=(1, 2), point_irrep=0, n_sublat=4, J1=1.0, J2=0.5, n_up=5),
+    w.tilted_square_40(momentum=(0, 0), point_irrep=0, n_sublat=4, J1=1.0, J2=0.0, n_up=4),
+], ids=lambda p: f"{p.name}_up{p.n_up}")
+def test_full_lattices_at_low_filling_every_row(p):
+    """The tables of the 6x6 torus (288 elements) and of the 40-site cluster depend on the
+    lattice and the group, not on n_up; at low filling the sectors are small enough to
+    check every row against the oracle, through the same kernel and tables (level 2 in
+    global memory) that the half-filled sectors use."""
+    import paper_1804_05028_gb300 as ed
+    B = ed.build_basis_from(p)
+    D = B.dim
+    assert D == oracle.dimension_formula(p) and D > 0
+    s, t = B.export()
+    assert np.all(s[1:] > s[:-1]) and np.all(_popcount(s) == p.n_up)
+    rep, g, stab, kept = oracle.representatives(p, s)
+    assert np.array_equal(rep, s) and np.all(kept) and np.array_equal(stab, t.astype(np.int32))
+    cplx = not p.is_real()
+    x = w.state_uniform(s, 1804)
+    xf = (lambda q: w.state_uniform(q, 1804))
+    if cplx:
+        x = x + 1j * w.state_uniform(s, 1805)
+        xf = (lambda q: w.state_uniform(q, 1804) + 1j * w.state_uniform(q, 1805))
+    y_ref = oracle.rows(p, s, xf)
+    scale = np.abs(y_ref).max()
+    dt = torch.complex128 if cplx else torch.float64
+    y = B.apply_H(torch.from_numpy(x).to(dt).cuda()).cpu().numpy()
+    assert np.abs(y - y_ref).max() <= 1e-12 * scale
+    x32 = x.astype(np.complex64 if cplx else np.float32)
+    y32 = B.apply_H(torch.from_numpy(x32).cuda()).cpu().numpy()
+    xf32 = (lambda q: xf(q).astype(x32.dtype).astype(np.complex128 if cplx else np.float64))
+    y_ref32 = oracle.rows(p, s, xf32)
+    assert np.abs(y32 - y_ref32).max() <= 2e-6 * scale
+    B.close()
