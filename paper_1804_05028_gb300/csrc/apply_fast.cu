@@ -1,5 +1,5 @@
-// apply_fast.cu -- the row-pull product y = H x with a two-level representative search
-// and several exchange terms in flight per thread.
+// apply_fast.cu -- the row-pull product y = H x with a two-level representative search,
+// one thread per row and one exchange term at a time.
 //
 // Two-level search.  In Alg. 2 of arXiv:1804.05028 the candidates of a minimal block Y
 // are Sym_Y(s_Y) = K_R h: the coset of the stabiliser K_R = {k in G_0 : k R = R} of
@@ -17,8 +17,8 @@
 // 32-bit masks (one coupling class per word); each exchange flips one bit in the block of
 // each end.  Tables: Rep_X / first of Sym_X, stabiliser ids, the level-2 tables (when
 // they fit), prefix ranks, bonds and norms in shared memory; SymmetryAction_X in global
-// memory (L1/L2).  The index of the representative: prefix rank, Limits bucket, binary
-// search of the narrow postfixes.  fp32 vectors are summed per row with a compensated
+// memory (L1/L2), and the level-2 tables there too when they do not fit.  The index of
+// the representative: prefix rank, Limits bucket, binary search of the narrow postfixes.  fp32 vectors are summed per row with a compensated
 // (two-float) accumulator, fp64 in fp64.  Each y_i written once; no atomics.
 #include "sced_internal.cuh"
 #include <algorithm>
