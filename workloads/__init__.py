@@ -40,6 +40,7 @@ __all__ = [
     "point_group_irreps", "momenta", "state_uniform", "state_gaussian",
     "splitmix64", "config_chain16", "config_square36", "config_square25_sectors",
     "config_tilted40", "C4V_OPS", "C4V_NAMES", "n_point_irreps", "with_spin_flip",
+    "to_dict", "from_dict",
 ]
 
 
@@ -81,6 +82,30 @@ class Problem:
         J = tuple(float(v) for v in J)
         Jz = tuple(float(v) for v in (Jz if Jz is not None else self.Jz))
         return dataclasses.replace(self, J=J, Jz=Jz)
+
+
+def to_dict(p: Problem) -> dict:
+    """A JSON-ready description of the sector: every field of Problem as plain lists."""
+    arr = lambda a: None if a is None else np.asarray(a).tolist()
+    return {"name": p.name, "n_sites": int(p.n_sites), "n_sublat": int(p.n_sublat),
+            "bonds": arr(p.bonds), "bond_class": arr(p.bond_class), "n_classes": int(p.n_classes),
+            "perm": arr(p.perm), "phase_denom": int(p.phase_denom), "phase_num": arr(p.phase_num),
+            "n_up": int(p.n_up), "J": [float(v) for v in p.J], "Jz": [float(v) for v in p.Jz],
+            "coords": arr(p.coords), "sym_names": None if p.sym_names is None else list(p.sym_names),
+            "flip": arr(p.flip)}
+
+
+def from_dict(d: dict) -> Problem:
+    """The inverse of to_dict."""
+    opt = lambda k, dt: None if d.get(k) is None else np.asarray(d[k], dtype=dt)
+    return Problem(name=str(d["name"]), n_sites=int(d["n_sites"]), n_sublat=int(d["n_sublat"]),
+                   bonds=np.asarray(d["bonds"], np.int32).reshape(-1, 2),
+                   bond_class=np.asarray(d["bond_class"], np.int32), n_classes=int(d["n_classes"]),
+                   perm=np.asarray(d["perm"], np.int32).reshape(-1, int(d["n_sites"])),
+                   phase_denom=int(d["phase_denom"]), phase_num=np.asarray(d["phase_num"], np.int32),
+                   n_up=int(d["n_up"]), J=tuple(float(v) for v in d["J"]),
+                   Jz=tuple(float(v) for v in d["Jz"]), coords=opt("coords", np.float64),
+                   sym_names=d.get("sym_names"), flip=opt("flip", np.uint8))
 
 
 def with_spin_flip(p: Problem, parity: int) -> Problem:
