@@ -124,7 +124,11 @@ typedef struct {
  *   opts: NULL or tuning.  stream: enqueue on this stream; the call is synchronous.
  *   out: receives the new basis (free with ed_free_basis), NULL on error.
  * A sector of dimension 0 is valid: *out is a basis with dim 0.
- * Errors: ED_ERR_INVALID, ED_ERR_UNSTABLE, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_UNSUPPORTED.
+ * Errors: ED_ERR_INVALID (malformed descriptor: not a group, characters not a
+ * homomorphism, bonds not invariant, n_up out of range, spin flip away from n_up = N/2),
+ * ED_ERR_UNSTABLE (n_sublat does not divide N, or a group element splits a block),
+ * ED_ERR_UNSUPPORTED (blocks above 20 sites, one block above 26 sites, dimension of
+ * 2^32 or more), ED_ERR_OOM, ED_ERR_CUDA.
  */
 int ed_build_basis(const ed_lattice *lattice, const ed_group *group, const ed_irrep *irrep,
                    int32_t n_up, const ed_basis_opts *opts, void *stream, ed_basis **out);
