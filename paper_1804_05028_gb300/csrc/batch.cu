@@ -78,6 +78,39 @@ __device__ __forceinline__ int sector_of(const BatchParams &P, int64_t item) {
 
 constexpr int kBatchThreads = 256;
 
+// Index of a representative of a sector with at most 26 sites (whole-table sectors):
+// the Limits lookup and bucket search of Sec. IV in 32-bit arithmetic.
+__device__ __forceinline__ int64_t lookup_index32(const DevIndex &I, uint32_t s) {
+  const uint32_t rk = __ldg(I.top_rank + (s >> (I.N - I.r_bits)));
+  if (rk == ED_NO_RANK) return -1;
+  const uint32_t key = (rk << I.q_bits) | ((s >> I.post_bits) & ((1u << I.q_bits) - 1u));
+  uint32_t lo = __ldg(I.limits + key), hi = __ldg(I.limits + key + 1);
+  const uint32_t p = s & ((1u << I.post_bits) - 1u);
+  const uint32_t end = hi;
+  if (I.post_bytes == 1) {
+    const uint8_t *post = reinterpret_cast<const uint8_t *>(I.postfix);
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if ((uint32_t)__ldg(post + mid) < p) lo = mid + 1; else hi = mid;
+    }
+    return (lo < end && (uint32_t)__ldg(post + lo) == p) ? (int64_t)lo : -1;
+  }
+  if (I.post_bytes == 2) {
+    const uint16_t *post = reinterpret_cast<const uint16_t *>(I.postfix);
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if ((uint32_t)__ldg(post + mid) < p) lo = mid + 1; else hi = mid;
+    }
+    return (lo < end && (uint32_t)__ldg(post + lo) == p) ? (int64_t)lo : -1;
+  }
+  const uint32_t *post = reinterpret_cast<const uint32_t *>(I.postfix);
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(post + mid) < p) lo = mid + 1; else hi = mid;
+  }
+  return (lo < end && __ldg(post + lo) == p) ? (int64_t)lo : -1;
+}
+
 // Eight fp32 values (32 bytes, 32-byte aligned) in one 256-bit load: a gathered row of
 // k >= 8 real or k >= 4 complex entries then costs one L1 request per lane, not two.
 struct F8 { float v[8]; };
@@ -148,7 +181,7 @@ __global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 5) : 1)
             R = find_rep(S.T, S.T.rep, S.T.sym_off, S.T.sym_list, S.T.dest, S.T.phase, s2);
             if (R.mixed) continue;
           }
-          const int64_t j = lookup_index(S.I, R.rep);
+          const int64_t j = kFull ? lookup_index32(S.I, (uint32_t)R.rep) : lookup_index(S.I, R.rep);
           if (j < 0) continue;
           float w = jh;
           if (R.t != 1) w *= __ldg(S.sqrt_f + R.t);   // t = |Stab| of the target, mostly 1
