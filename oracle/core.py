@@ -15,6 +15,7 @@ __all__ = [
     "build", "lib", "OracleProblem", "representatives", "basis", "columns",
     "hamiltonian", "apply", "rows", "dimension_formula", "projected_hamiltonian",
     "full_hamiltonian", "lanczos", "sublattice_tables", "apply_sym", "max_threads",
+    "StoredMatrix", "stored_matrix",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -58,6 +59,9 @@ def lib():
             L.or_basis.restype = i64
             L.or_columns.argtypes = [P, vp, i64, vp, vp, vp, vp, vp]
             L.or_max_threads.restype = ctypes.c_int
+            L.or_rows_slots.argtypes = [P, vp, vp, i64, i64, i64, vp, vp, vp, vp, vp]
+            L.or_csr_spmv.argtypes = [i64, vp, vp, vp, vp, vp, vp, i64]
+            L.or_csr_spmv_complex.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, i64]
             _lib = L
     return _lib
 
@@ -147,11 +151,11 @@ def columns(p, states):
     op = _op(p)
     s = np.ascontiguousarray(states, dtype=np.uint64)
     n, nb = s.size, op.p.n_bonds
-    diag = np.empty(n)
-    nt = np.empty(n, np.int32)
-    reps = np.empty(n * nb, np.uint64)
-    re = np.empty(n * nb)
-    im = np.empty(n * nb)
+    diag = np.zeros(n)
+    nt = np.zeros(n, np.int32)
+    reps = np.zeros(n * nb, np.uint64)
+    re = np.zeros(n * nb)
+    im = np.zeros(n * nb)
     lib().or_columns(op.ref, s.ctypes.data, n, diag.ctypes.data, nt.ctypes.data,
                      reps.ctypes.data, re.ctypes.data, im.ctypes.data)
     reps = reps.reshape(n, nb)
@@ -190,6 +194,87 @@ def hamiltonian(p, basis_states=None):
     if op.p.is_real():
         H = H.real.tocsr()
     return H, bs, stab
+
+
+class StoredMatrix:
+    """The symmetry-adapted Hamiltonian stored row by row (CSR), fp64.
+
+    Row i holds H[i][j] = conj(<j|H|i>) (Hermitian H: the conjugate of column i), in
+    bond order, duplicates not merged; the diagonal is kept apart.  Column indices are
+    uint32 (D < 2^32).  The rows are kept as consecutive row blocks, each its own CSR
+    (so that building never holds two copies of the entries).  ``matvec`` is the
+    stored-matrix product of Sec. IV.
+    """
+
+    def __init__(self, D, blocks, diag, cplx):
+        self.D, self.blocks, self.diag, self.cplx = D, blocks, diag, cplx
+
+    @property
+    def nnz(self) -> int:
+        """Stored off-diagonal entries (one per surviving exchange term)."""
+        return int(sum(b[2][-1] for b in self.blocks))
+
+    def matvec(self, x):
+        L = lib()
+        dt = np.complex128 if self.cplx else np.float64
+        x = np.ascontiguousarray(x, dtype=dt)
+        y = np.empty(self.D, dt)
+        es = y.itemsize
+        for r0, r1, rowptr, col, vre, vim in self.blocks:
+            yp = y.ctypes.data + r0 * es
+            dp = self.diag.ctypes.data + r0 * 8
+            if not self.cplx:
+                L.or_csr_spmv(r1 - r0, rowptr.ctypes.data, col.ctypes.data, vre.ctypes.data,
+                              dp, x.ctypes.data, yp, r0)
+            else:
+                L.or_csr_spmv_complex(r1 - r0, rowptr.ctypes.data, col.ctypes.data,
+                                      vre.ctypes.data, vim.ctypes.data, dp, x.ctypes.data, yp, r0)
+        return y
+
+
+def stored_matrix(p, basis_states=None, chunk_rows: int = 1 << 20, progress=None) -> StoredMatrix:
+    """Build the whole Hamiltonian of a sector as a :class:`StoredMatrix`.
+
+    Every exchange term's representative comes from applying every group element
+    (Eq. 4); its index is its position in the sorted oracle basis (binary search over
+    the whole array); a representative absent from the basis is one the projection
+    removes.  Rows are produced in blocks of ``chunk_rows`` (n_bonds slots per row,
+    then compacted), so the peak extra memory is one block of slots.
+    """
+    op = _op(p)
+    if basis_states is None:
+        bs, stab = basis(op.p)
+    else:
+        bs, stab = basis_states
+    bs = np.ascontiguousarray(bs, dtype=np.uint64)
+    stab = np.ascontiguousarray(stab, dtype=np.int32)
+    D, nb = bs.size, op.p.n_bonds
+    if D >= 1 << 32:
+        raise ValueError("dimension too large for uint32 column indices")
+    cplx = not op.p.is_real()
+    rows = min(chunk_rows, max(D, 1))
+    s_col = np.zeros(rows * nb, np.uint32)
+    s_re = np.zeros(rows * nb)
+    s_im = np.zeros(rows * nb) if cplx else None
+    s_nt = np.zeros(rows, np.int32)
+    diag = np.zeros(D)
+    blocks = []
+    L = lib()
+    for r0 in range(0, D, rows):
+        r1 = min(D, r0 + rows)
+        L.or_rows_slots(op.ref, bs.ctypes.data, stab.ctypes.data, D, r0, r1,
+                        diag[r0:r1].ctypes.data, s_nt.ctypes.data, s_col.ctypes.data,
+                        s_re.ctypes.data, None if s_im is None else s_im.ctypes.data)
+        n = r1 - r0
+        nt = s_nt[:n]
+        keep = (np.arange(nb, dtype=np.int32)[None, :] < nt[:, None]).ravel()
+        rowptr = np.zeros(n + 1, np.int64)
+        rowptr[1:] = np.cumsum(nt, dtype=np.int64)
+        blocks.append((r0, r1, rowptr, s_col[:n * nb][keep].copy(), s_re[:n * nb][keep].copy(),
+                       s_im[:n * nb][keep].copy() if cplx else None))
+        if progress:
+            progress(r1, D)
+    return StoredMatrix(D, blocks, diag, cplx)
 
 
 def apply(p, x, H=None):

@@ -50,7 +50,7 @@ static uint64_t apply_sym(const or_problem *P, int g, uint64_t s) {
   const int32_t *perm = P->perm + (size_t)g * P->N;
   uint64_t r = 0;
   for (int p = 0; p < P->N; p++)
-    if (spin(s, P->N, p)) r |= 1ULL << (P->N - 1 - perm[p]);
+    r |= (uint64_t)spin(s, P->N, p) << (P->N - 1 - perm[p]);
   if (P->flip && P->flip[g]) {
     const uint64_t all = (P->N == 64) ? ~0ULL : ((1ULL << P->N) - 1ULL);
     r ^= all;
@@ -202,6 +202,90 @@ void or_columns(const or_problem *P, const uint64_t *s, int64_t n, double *diag,
   for (int64_t r = 0; r < n; r++) {
     size_t o = (size_t)r * P->n_bonds;
     nterm[r] = or_column(P, s[r], &diag[r], rep_out + o, re_out + o, im_out + o);
+  }
+}
+
+/* Position of s in the sorted basis by binary search over the whole array (Sec. IV's
+ * Basis without a prefix map), or -1 when s is not in it. */
+static int64_t basis_index(const uint64_t *basis, int64_t D, uint64_t s) {
+  int64_t lo = 0, hi = D;
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (basis[mid] < s) lo = mid + 1; else hi = mid;
+  }
+  return (lo < D && basis[lo] == s) ? lo : -1;
+}
+
+/* Rows [r0, r1) of the symmetry-adapted Hamiltonian as a stored sparse matrix (the
+ * stored-matrix alternative to the matrix-free product, Sec. IV).  Row i of the
+ * Hermitian H is the complex conjugate of column i:
+ *   H[i][j] = conj(<j|H_k|i>) = c chi(h) N_j / N_i,   s_j = h s',  s' = H_k s_i,
+ * with the representative s_j found by applying every group element (Eq. 4), and the
+ * target's position j its index in the sorted basis `basis` (found by binary search).
+ * A representative that is not in the basis is one the projection removes (its
+ * stabiliser carries a non-trivial character, Eq. 2): the term contributes nothing.
+ * |Stab(s_j)| is read from `stab`, the stabiliser orders that or_basis found for the
+ * same states.  Each row gets n_bonds slots starting at (i - r0) * n_bonds; nterm[i - r0]
+ * says how many are used, in bond order.  diag[i - r0] is the S^z S^z part (Eq. 21). */
+void or_rows_slots(const or_problem *P, const uint64_t *basis, const int32_t *stab, int64_t D,
+                   int64_t r0, int64_t r1, double *diag, int32_t *nterm, uint32_t *col,
+                   double *re, double *im) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = r0; i < r1; i++) {
+    const uint64_t s_i = basis[i];
+    const size_t o = (size_t)(i - r0) * (size_t)P->n_bonds;
+    double d = 0.0;
+    int32_t nt = 0;
+    for (int b = 0; b < P->n_bonds; b++) {
+      const int a = P->bonds[2 * b], c = P->bonds[2 * b + 1];
+      const int cls = P->bond_class[b];
+      if (spin(s_i, P->N, a) == spin(s_i, P->N, c)) { d += 0.25 * P->J[cls] * P->Jz[cls]; continue; }
+      d -= 0.25 * P->J[cls] * P->Jz[cls];
+      const uint64_t sp = s_i ^ (1ULL << (P->N - 1 - a)) ^ (1ULL << (P->N - 1 - c));
+      uint64_t rep;
+      int32_t h, nm;
+      representative(P, sp, &rep, &h, &nm);
+      const int64_t j = basis_index(basis, D, rep);
+      if (j < 0) continue;
+      const double amp = 0.5 * P->J[cls] * sqrt((double)stab[j] / (double)stab[i]);
+      const double ph = 2.0 * M_PI * (double)P->phase_num[h] / (double)P->phase_denom;
+      col[o + nt] = (uint32_t)j;
+      re[o + nt] = amp * cos(ph);
+      if (im) im[o + nt] = amp * sin(ph);
+      nt++;
+    }
+    diag[i - r0] = d;
+    nterm[i - r0] = nt;
+  }
+}
+
+/* y = H x for n consecutive rows r0 .. r0+n-1 of H stored row by row (CSR: row r0+i
+ * holds entries rowptr[i] .. rowptr[i+1]), real entries, fp64; diag and y point at
+ * the block's first row, x is the whole vector.  Rows are independent. */
+void or_csr_spmv(int64_t n, const int64_t *rowptr, const uint32_t *col, const double *val,
+                 const double *diag, const double *x, double *y, int64_t r0) {
+#pragma omp parallel for schedule(static, 4096)
+  for (int64_t i = 0; i < n; i++) {
+    double acc = diag[i] * x[r0 + i];
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) acc += val[k] * x[col[k]];
+    y[i] = acc;
+  }
+}
+
+/* The same for complex entries and vectors, interleaved (re, im). */
+void or_csr_spmv_complex(int64_t n, const int64_t *rowptr, const uint32_t *col,
+                         const double *vre, const double *vim, const double *diag,
+                         const double *x, double *y, int64_t r0) {
+#pragma omp parallel for schedule(static, 4096)
+  for (int64_t i = 0; i < n; i++) {
+    double ar = diag[i] * x[2 * (r0 + i)], ai = diag[i] * x[2 * (r0 + i) + 1];
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) {
+      const double xr = x[2 * col[k]], xi = x[2 * col[k] + 1];
+      ar += vre[k] * xr - vim[k] * xi;
+      ai += vre[k] * xi + vim[k] * xr;
+    }
+    y[2 * i] = ar;
+    y[2 * i + 1] = ai;
   }
 }
 
