@@ -148,38 +148,57 @@ def sector_bytes(D: int, n_off: int, vec_bytes: int) -> int:
     return D * (8 + 2 + 2 * vec_bytes) + n_off * 32
 
 
-def cpu_baseline(p, states, seconds: float, seed: int = 7):
+def oracle_sample(p, n_cfg: int, seed: int):
+    """Representatives of the sector found by the oracle itself: random configurations with
+    n_up up spins, their brute-force representatives, the surviving ones, sorted and
+    unique (the oracle cannot enumerate C(36,18) configurations in a bench run)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    N, n_up = p.n_sites, p.n_up
+    cfg = np.zeros(n_cfg, np.uint64)
+    for a in range(0, n_cfg, 1 << 16):           # n_up distinct sites per configuration
+        m = min(n_cfg, a + (1 << 16)) - a
+        sites = np.argsort(rng.random((m, N)), axis=1)[:, :n_up].astype(np.uint64)
+        cfg[a:a + m] = np.bitwise_or.reduce(np.uint64(1) << sites, axis=1)
+    rep, _, _, kept = oracle.representatives(p, cfg)
+    return np.unique(rep[kept])
+
+
+def cpu_baseline(p, seconds: float, seed: int = 7):
     """The oracle's matrix-free rows (brute-force representatives) on a sample of rows,
     sized to about `seconds` of work on the host cores."""
     import oracle
-    rng = np.random.default_rng(seed)
     xf = lambda q: workloads.state_uniform(q, 1804)
-    oracle.rows(p, states[:16], xf)            # load the library, start the thread pool
+    reps = oracle_sample(p, 1 << 18, seed)
+    reps = reps[np.random.default_rng(seed).permutation(reps.size)]   # unbiased prefixes
+    oracle.rows(p, reps[:16], xf)              # load the library, start the thread pool
     n, dt = 64, 0.0
     while True:                                # grow the calibration sample to >= 1 s
-        pick = np.sort(rng.choice(states.size, min(n, states.size), replace=False))
+        pick = reps[:min(n, reps.size)]
         t0 = time.perf_counter()
-        oracle.rows(p, states[pick], xf)
+        oracle.rows(p, pick, xf)
         dt = time.perf_counter() - t0
-        if dt >= 1.0 or n >= states.size:
+        if dt >= 1.0 or n >= reps.size:
             break
         n *= 4
-    n = int(min(states.size, max(64, n * seconds / max(dt, 1e-3))))
-    pick = np.sort(rng.choice(states.size, n, replace=False))
+    n = int(min(reps.size, max(64, n * seconds / max(dt, 1e-3))))
+    pick = reps[:n]
     t0 = time.perf_counter()
-    oracle.rows(p, states[pick], xf)
+    oracle.rows(p, pick, xf)
     dt = time.perf_counter() - t0
-    _, nt, _, _ = oracle.columns(p, states[pick])
+    _, nt, _, _ = oracle.columns(p, pick)
     nnz = int(n + nt.sum())
     return {"value": nnz / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{n} rows of {states.size} (matrix-free brute-force rows, fp64), {nnz} nonzeros in {dt:.1f}s"}
+            "sample": f"{n} representatives found by the oracle from random configurations "
+                      f"(matrix-free brute-force rows, fp64), {nnz} nonzeros in {dt:.1f}s"}
 
 
 def bench_batch(ed, torch, steps: int):
     """All 572 sectors of the 5x5 J1-J2 torus (S^z = 1/2 .. 25/2, every momentum and
     little-group 1-D irrep) in one persistent, graph-replayed launch with block vectors
-    k = 1, 4, 8 (fp32 / complex fp32, Gaussian).  Returns per-k throughput in
-    nonzero-vector products per second."""
+    k = 1, 4, 8 (fp32 / complex fp32, Gaussian), and the same work through the plain
+    per-sector product (ed_apply_H once per sector and vector, fp32 and fp64).  Returns
+    per-k throughput in nonzero-vector products per second."""
     t0 = time.time()
     probs = workloads.config_square25_sectors(0.3)
     bases = ed.build_sectors(probs)
@@ -199,6 +218,7 @@ def bench_batch(ed, torch, steps: int):
            "l2": "inputs larger than L2: 6 whole-lattice tables of 268 MB each, basis %d MB"
                  % (sum(d for d, _, _ in per) * 8 >> 20)}
     g = torch.Generator(device="cuda").manual_seed(1804)
+    nz = [B for B in bases if B.dim]
     for k in (1, 4, 8):
         xs = [torch.randn(B.dim * k, dtype=torch.float32 if B.is_real else torch.complex64,
                           device="cuda", generator=g) for B in bases]
@@ -219,12 +239,40 @@ def bench_batch(ed, torch, steps: int):
         # per row: state, |Stab|, k entries of x_i and y_i; per term: k gathered entries
         ab = sum(d * (8 + 2 + 2 * k * b) + t * k * b for d, t, b in per)
         ach = ab / (ms * 1e-3) / 1e9
+        # the same work through the plain per-sector product: k separate vectors per sector
+        plain = {}
+        cols = [(B, x.view(B.dim, k)) for B, x in zip(bases, xs) if B.dim]
+        for name, real_dt, cplx_dt in (("f32", torch.float32, torch.complex64),
+                                       ("f64", torch.float64, torch.complex128)):
+            vx = [[X[:, v].contiguous().to(real_dt if B.is_real else cplx_dt) for v in range(k)]
+                  for B, X in cols]
+            vy = [[torch.empty_like(c) for c in row] for row in vx]
+            def run():
+                for (B, _), xr, yr in zip(cols, vx, vy):
+                    for xc, yc in zip(xr, yr):
+                        B.apply_H(xc, yc)
+            run()
+            torch.cuda.synchronize()
+            reps = max(1, steps // 4)
+            e0.record()
+            for _ in range(reps):
+                run()
+            e1.record()
+            torch.cuda.synchronize()
+            plain[name] = e0.elapsed_time(e1) / reps
+            del vx, vy
         out[f"k{k}"] = {"ms_per_apply": ms, "value": nnz * k / (ms * 1e-3),
                         "unit": "nonzero-vector products/s", **bt.info(),
+                        "plain_f32_ms": plain["f32"], "plain_f64_ms": plain["f64"],
+                        "batched_ms": ms,
+                        "speedup_vs_plain_f32": plain["f32"] / ms,
+                        "speedup_vs_plain_f64": plain["f64"] / ms,
+                        "plain": f"ed_apply_H per sector and vector: {len(nz) * k} launches",
                         "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                                      "frac": ach / pk["hbm_gbs"], "peak_kind": pk_kind,
                                      "alg_bytes_per_launch": ab}}
         bt.close()
+        del xs, ys
     for B in bases:
         B.close()
     return out
@@ -238,15 +286,10 @@ def run_reference(args):
     import oracle
     desc, mk = WORKLOADS[args.workload]
     p = mk()
-    # representatives of the sector from the oracle itself: sample configurations and
-    # keep their representatives (the oracle cannot enumerate C(36,18) states)
+    # representatives of the sector from the oracle itself (it cannot enumerate C(36,18)
+    # configurations)
     rng = np.random.default_rng(11)
-    N, n_up = p.n_sites, p.n_up
-    cfg = np.zeros(4096, np.uint64)
-    for i in range(cfg.size):
-        cfg[i] = np.bitwise_or.reduce(np.uint64(1) << rng.choice(N, n_up, replace=False).astype(np.uint64))
-    rep, _, _, kept = oracle.representatives(p, cfg)
-    reps = np.unique(rep[kept])
+    reps = oracle_sample(p, 4096, 11)
     xf = lambda q: workloads.state_uniform(q, 1804)
     # calibrate rows per step to about one second
     oracle.rows(p, reps[:16], xf)
@@ -279,6 +322,126 @@ def run_reference(args):
     return 0
 
 
+def bench_sector(ed, torch, workload, p, steps, warmup, ctx, accuracy=True, full_reorth=False):
+    """Lanczos steps on one sector, fp64 and mixed (fp32 vectors, fp64 scalars and local
+    reorthogonalisation): per-step throughput, the product's roofline, the accuracy of the
+    mixed form against fp64, and the end-to-end product through the host-buffer entry
+    point.  With full_reorth the mixed accuracy run is repeated with the whole Krylov
+    basis stored and reorthogonalised against."""
+    world, rank, barrier, allmax = ctx["world"], ctx["rank"], ctx["barrier"], ctx["allmax"]
+    B = ed.build_basis_from(p)
+    info = B.info()
+    D = info["dim"]
+    n_flip, n_off = B.count_terms()
+    nnz = D + n_off
+
+    # accuracy of the mixed form against fp64 (untimed): full Lanczos runs to convergence
+    acc = {}
+    if accuracy:
+        want_psi = D < 1e8   # the ground state costs a second pass; skip it on the 40-site sector
+        psi64 = torch.empty(D, dtype=torch.float64, device="cuda") if want_psi else None
+        r64 = B.lanczos(dtype=torch.float64, max_steps=400, psi=psi64)
+        del psi64
+        psi32 = torch.empty(D, dtype=torch.float32, device="cuda") if want_psi else None
+        r32 = B.lanczos(dtype=torch.float32, max_steps=400, psi=psi32)
+        acc = {"E0_f64": r64["E0"], "steps_f64": r64["steps"],
+               "E0_mixed": r32["E0"], "steps_mixed": r32["steps"],
+               "dE0_rel_mixed": abs(r32["E0"] - r64["E0"]) / abs(r64["E0"]),
+               "reorth": "local (second Gram-Schmidt sweep against v_j, v_j-1, fp64 dots)"}
+        if want_psi:
+            acc.update({"rq_f64": r64["rq"], "rq_mixed": r32["rq"],
+                        "dE0_rel_mixed_rq": abs(r32["rq"] - r64["E0"]) / abs(r64["E0"]),
+                        "dE0_rel_f64_rq": abs(r64["rq"] - r64["E0"]) / abs(r64["E0"])})
+        if full_reorth:
+            m = r32["steps"] + 1
+            kry = torch.empty((m + 1) * D, dtype=torch.float32, device="cuda")
+            psi32 = torch.empty(D, dtype=torch.float32, device="cuda")
+            rf = B.lanczos(dtype=torch.float32, max_steps=m, psi=psi32, reorth="full", krylov=kry)
+            acc["full_reorth_mixed"] = {
+                "E0": rf["E0"], "steps": rf["steps"], "rq": rf["rq"],
+                "dE0_rel": abs(rf["E0"] - r64["E0"]) / abs(r64["E0"]),
+                "dE0_rel_rq": abs(rf["rq"] - r64["E0"]) / abs(r64["E0"]),
+                "reorth_ms_per_step": rf["ms_reorth"] / rf["steps"],
+                "apply_ms_per_step": rf["ms_apply"] / rf["steps"],
+                "store_bytes": kry.numel() * 4}
+            del kry, psi32
+
+    pk, pk_kind = peaks()
+    n_sm = ctx["n_sm"]
+    results = {}
+    for name, dt, vb in (("f64", torch.float64, 8), ("mixed", torch.float32, 4)):
+        work = torch.empty(3 * D, dtype=dt, device="cuda")
+        B.lanczos(dtype=dt, fixed_steps=max(warmup, 1), work=work)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(ctx["local"]) as cs:
+            e0.record()
+            r = B.lanczos(dtype=dt, fixed_steps=steps, work=work)
+            e1.record()
+            torch.cuda.synchronize()
+        barrier()
+        ms = allmax(e0.elapsed_time(e1))
+        apply_ms = r["ms_apply"] / steps
+        ab = alg_bytes(D, n_off, vb)
+        achieved = ab / (apply_ms * 1e-3) / 1e9
+        clk = cs.summary()
+        # instruction-issue roof: every SM issues at most one warp instruction per cycle on
+        # each of its 4 schedulers, at the SM clock sampled during the timed region
+        winst = profiled(workload, "warp_instructions_per_launch", name)
+        issue_peak = 4 * n_sm * clk["sm_mhz"] * 1e6 / 1e9 if clk.get("sm_mhz") else None
+        issue = None
+        if winst is not None and issue_peak:
+            ia = winst / (apply_ms * 1e-3) / 1e9
+            issue = {"bound": "issue", "achieved": ia, "peak": issue_peak, "unit": "Gwarp-inst/s",
+                     "frac": ia / issue_peak, "warp_instructions_per_launch": winst,
+                     "peak_kind": f"4 schedulers x {n_sm} SMs x sampled SM clock"}
+        results[name] = {
+            "value": world * nnz * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "apply_ms": apply_ms, "reorth_ms": r["ms_reorth"] / steps, "clocks": clk,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
+                         "traffic": profiled(workload, "traffic_bytes_per_launch", name),
+                         "alg_bytes_per_launch": ab,
+                         "sector_bytes_per_launch": sector_bytes(D, n_off, vb)},
+            "roofline_issue": issue,
+            # per step: product, three-term update, scale, and the local sweep's
+            # multi-dot, coefficient reduction and update
+            "gpu_launches": 6 * steps + 2,
+        }
+        del work
+
+    ok_mixed = (not acc) or acc["dE0_rel_mixed"] <= 1e-9
+    head_name = "mixed" if ok_mixed else "f64"
+
+    # end to end through the host-buffer entry point: H2D of x, product, D2H of y per step
+    hd = torch.float32 if ok_mixed else torch.float64
+    xh = torch.from_numpy(workloads.state_uniform(B.export()[0], 1804)).to(hd).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(max(warmup, 1)):
+        B.apply_H_host(xh, yh)
+    barrier()
+    e2e_steps = max(2, steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        B.apply_H_host(xh, yh)
+    torch.cuda.synchronize()
+    t_e2e = allmax(time.perf_counter() - t0)
+    eb = xh.numel() * xh.element_size()
+    e2e = {"value": world * nnz * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": eb,
+           "d2h_bytes_per_step": eb, "ms_per_step": 1000 * t_e2e / e2e_steps, "steps": e2e_steps,
+           "what": "ed_apply_H_host: pinned host x -> device, product, device -> pinned host y"}
+    del xh, yh
+    cfg = {"dim": D, "offdiag_terms_per_product": n_off, "exchange_terms_per_product": n_flip,
+           "nonzeros_per_product": nnz, "n_sublat": p.n_sublat, "n_sym": p.n_sym,
+           "step": "one Lanczos iteration (apply_H with fused <v,Hv>, update with ||w||, "
+                   "local reorthogonalisation sweep, scale)",
+           "l2": "inputs larger than L2: basis %d MB, each vector %d MB" % (D * 8 >> 20, D * (4 if head_name == 'mixed' else 8) >> 20),
+           "index": {k: info[k] for k in ("prefix_rank_bits", "prefix_raw_bits", "postfix_bits", "n_keys", "max_bucket")},
+           "basis_build_ms": info["build_ms"], "steps": steps}
+    B.close()
+    return {"results": results, "headline": head_name, "accuracy": acc, "e2e": e2e, "config": cfg}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,6 +453,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 40-site sector that the default run adds as 'large'")
     ap.add_argument("--batch-only", action="store_true",
                     help="time only the batched 5x5 sectors and print their JSON object")
     args = ap.parse_args()
@@ -329,120 +494,44 @@ def main():
     desc, mk = WORKLOADS[args.workload]
     p = mk()
     ed.build()
-    B = ed.build_basis_from(p)
-    info = B.info()
-    D = info["dim"]
-    n_flip, n_off = B.count_terms()
-    nnz = D + n_off
-
-    # accuracy of the mixed form against fp64 (untimed): full Lanczos runs to convergence
-    acc = {}
-    if not args.no_accuracy:
-        psi64 = torch.empty(D, dtype=torch.float64, device="cuda")
-        r64 = B.lanczos(dtype=torch.float64, max_steps=400, psi=psi64)
-        del psi64
-        psi32 = torch.empty(D, dtype=torch.float32, device="cuda")
-        r32 = B.lanczos(dtype=torch.float32, max_steps=400, psi=psi32)
-        acc = {"E0_f64": r64["E0"], "steps_f64": r64["steps"], "rq_f64": r64["rq"],
-               "E0_mixed": r32["E0"], "steps_mixed": r32["steps"], "rq_mixed": r32["rq"],
-               "dE0_rel_mixed": abs(r32["E0"] - r64["E0"]) / abs(r64["E0"]),
-               "dE0_rel_mixed_rq": abs(r32["rq"] - r64["E0"]) / abs(r64["E0"]),
-               "dE0_rel_f64_rq": abs(r64["rq"] - r64["E0"]) / abs(r64["E0"])}
-        del psi32
-
-    pk, pk_kind = peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    results = {}
-    for name, dt, vb in (("f64", torch.float64, 8), ("mixed", torch.float32, 4)):
-        work = torch.empty(3 * D, dtype=dt, device="cuda")
-        B.lanczos(dtype=dt, fixed_steps=max(args.warmup, 1), work=work)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as cs:
-            e0.record()
-            r = B.lanczos(dtype=dt, fixed_steps=args.steps, work=work)
-            e1.record()
-            torch.cuda.synchronize()
-        barrier()
-        ms = allmax(e0.elapsed_time(e1))
-        apply_ms = r["ms_apply"] / args.steps
-        ab = alg_bytes(D, n_off, vb)
-        achieved = ab / (apply_ms * 1e-3) / 1e9
-        clk = cs.summary()
-        # instruction-issue roof: every SM issues at most one warp instruction per cycle on
-        # each of its 4 schedulers, at the SM clock sampled during the timed region
-        winst = profiled(args.workload, "warp_instructions_per_launch", name)
-        issue_peak = 4 * n_sm * clk["sm_mhz"] * 1e6 / 1e9 if clk.get("sm_mhz") else None
-        issue = None
-        if winst is not None and issue_peak:
-            ia = winst / (apply_ms * 1e-3) / 1e9
-            issue = {"bound": "issue", "achieved": ia, "peak": issue_peak, "unit": "Gwarp-inst/s",
-                     "frac": ia / issue_peak, "warp_instructions_per_launch": winst,
-                     "peak_kind": "4 x SMs x sampled SM clock"}
-        results[name] = {
-            "value": world * nnz * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
-            "apply_ms": apply_ms, "clocks": clk,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
-                         "traffic": profiled(args.workload, "traffic_bytes_per_launch", name),
-                         "alg_bytes_per_launch": ab,
-                         "sector_bytes_per_launch": sector_bytes(D, n_off, vb)},
-            "roofline_issue": issue,
-            "gpu_launches": 3 * args.steps + 2,
-        }
-        del work
-
-    ok_mixed = (not acc) or acc["dE0_rel_mixed"] <= 1e-9
-    head = results["mixed"] if ok_mixed else results["f64"]
-    head_name = "mixed" if ok_mixed else "f64"
-
-    # end to end through the host-buffer entry point: H2D of x, product, D2H of y per step
-    e2e = None
-    if rank == 0 or world > 1:
-        hd = torch.float32 if ok_mixed else torch.float64
-        xh = torch.from_numpy(workloads.state_uniform(B.export()[0], 1804)).to(hd).pin_memory()
-        yh = torch.empty_like(xh).pin_memory()
-        for _ in range(max(args.warmup, 1)):
-            B.apply_H_host(xh, yh)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            B.apply_H_host(xh, yh)
-        torch.cuda.synchronize()
-        t_e2e = allmax(time.perf_counter() - t0)
-        eb = xh.numel() * xh.element_size()
-        e2e = {"value": world * nnz * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": eb,
-               "d2h_bytes_per_step": eb, "ms_per_step": 1000 * t_e2e / args.steps,
-               "what": "ed_apply_H_host: pinned host x -> device, product, device -> pinned host y"}
+    ctx = {"world": world, "rank": rank, "local": local, "barrier": barrier, "allmax": allmax,
+           "n_sm": n_sm}
+    main_res = bench_sector(ed, torch, args.workload, p, args.steps, args.warmup, ctx,
+                            accuracy=not args.no_accuracy, full_reorth=True)
 
     batch = None
     if not args.no_batch and args.workload == "square36":
         batch = bench_batch(ed, torch, max(args.steps, 5))
 
+    large = None
+    if not args.no_large and args.workload == "square36":
+        _, mk40 = WORKLOADS["tilted40"]
+        large = bench_sector(ed, torch, "tilted40", mk40(), max(2, args.steps // 6),
+                             max(1, min(args.warmup, 2)), ctx, accuracy=not args.no_accuracy,
+                             full_reorth=False)
+        large = {"workload": "tilted40", "description": WORKLOADS["tilted40"][0], **large}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, B.export()[0], args.cpu_seconds)
+        cpu = cpu_baseline(p, args.cpu_seconds)
 
     if rank == 0:
+        r = main_res
+        head = r["results"][r["headline"]]
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 vectors / f64 scalars" if head_name == "mixed" else "f64",
+            "dtype": "f32 vectors / f64 scalars" if r["headline"] == "mixed" else "f64",
             "data": "synthetic (state-keyed uniform[-1,1) start vector, seed 1805)",
-            "config": {"workload": args.workload, "description": desc, "dim": D,
-                       "offdiag_terms_per_product": n_off, "exchange_terms_per_product": n_flip,
-                       "nonzeros_per_product": nnz, "n_sublat": p.n_sublat, "n_sym": p.n_sym,
-                       "step": "one Lanczos iteration (apply_H with fused <v,Hv>, update with ||w||, scale)",
-                       "l2": "inputs larger than L2: basis %d MB, each vector %d MB" % (D * 8 >> 20, D * (4 if head_name == 'mixed' else 8) >> 20),
-                       "index": {k: info[k] for k in ("prefix_rank_bits", "prefix_raw_bits", "postfix_bits", "n_keys", "max_bucket")},
-                       "basis_build_ms": info["build_ms"],
+            "config": {"workload": args.workload, "description": desc, **r["config"],
                        "parallelism": f"replicas x{world}"},
             "roofline": head["roofline"], "roofline_issue": head["roofline_issue"],
             "clocks": head["clocks"], "gpu_launches": head["gpu_launches"],
-            "e2e": e2e, "cpu_baseline": cpu, "headline": head_name,
-            "fp64": results["f64"], "mixed": results["mixed"], "accuracy": acc, "batch": batch,
-            "kernel_sha": kernel_hash(),
+            "e2e": r["e2e"], "cpu_baseline": cpu, "headline": r["headline"],
+            "fp64": r["results"]["f64"], "mixed": r["results"]["mixed"], "accuracy": r["accuracy"],
+            "batch": batch, "large": large, "n_sm": n_sm, "kernel_sha": kernel_hash(),
         }
         print(json.dumps(line))
     if dist:

@@ -196,6 +196,15 @@ int ed_apply_H_rows(const ed_basis *basis, const double *J, const double *Jz, co
 int ed_apply_H_host(ed_basis *basis, const double *J, const double *Jz, const void *x_host,
                     void *y_host, int32_t dtype, void *stream);
 
+/* Reorthogonalisation of the Lanczos vectors (ed_lanczos_opts.reorth).  Every dot,
+ * coefficient and update of a sweep is accumulated in double, whatever the vector type. */
+#define ED_REORTH_LOCAL 0  /* default: after the three-term update, one more Gram-Schmidt sweep
+                              against v_j and v_{j-1} (two extra dots, one extra update) */
+#define ED_REORTH_NONE 1   /* the plain three-term recurrence */
+#define ED_REORTH_FULL 2   /* two classical Gram-Schmidt sweeps against every earlier Lanczos
+                              vector, which the caller's Krylov store keeps; the ground state
+                              is then formed from the store, without a second pass */
+
 /* Lanczos options; zero-initialise and set what you need. */
 typedef struct {
   int32_t max_steps;          /* default 300 when 0 */
@@ -210,8 +219,9 @@ typedef struct {
   const void *v0;             /* optional DEVICE start vector (dtype, dim) */
   void *psi;                  /* optional DEVICE output (dtype, dim): normalised ground
                                  state from a second Lanczos pass */
-  double *alpha;              /* optional HOST output [max_steps] */
-  double *beta;               /* optional HOST output [max_steps] */
+  double *alpha;              /* optional HOST output of M doubles, where M = fixed_steps
+                                 when fixed_steps > 0, else max_steps, else 300 */
+  double *beta;               /* optional HOST output of M doubles (M as for alpha) */
   void *stream;
   void *work;                 /* optional DEVICE workspace of >= 3 * dim elements of dtype,
                                  caller-owned; when NULL the call allocates its own */
@@ -219,6 +229,13 @@ typedef struct {
   double tol_residual;        /* > 0: also require the Ritz residual beta_m |s_m| of the lowest
                                  pair to fall below tol_residual * max(1, |E0|) (for an
                                  accurate ground state, e.g. derivatives); 0: energy only */
+  int32_t reorth;             /* ED_REORTH_LOCAL (0), ED_REORTH_NONE or ED_REORTH_FULL */
+  int32_t reserved1;
+  void *krylov;               /* ED_REORTH_FULL only: caller-owned DEVICE store of krylov_bytes
+                                 bytes; slot k (dim elements of dtype, slot k at byte
+                                 k * dim * element size) receives v_k.  The run takes at most
+                                 min(slots - 1, 1024) steps; work is not used */
+  int64_t krylov_bytes;
 } ed_lanczos_opts;
 
 typedef struct {
@@ -230,15 +247,21 @@ typedef struct {
                                  requested (Rayleigh quotient), else 0 */
   double ms_total;            /* wall time */
   double ms_apply;            /* device time spent in apply_H (CUDA events) */
+  double ms_reorth;           /* device time spent in reorthogonalisation sweeps */
 } ed_lanczos_result;
 
 /*
  * ed_lanczos -- ground-state energy by the Lanczos iteration with apply_H as the
  * matrix-vector product (Sec. IV: the product dominates; dots, scalings and the
- * tridiagonal eigenproblem are cheap).  Three device vectors of dtype (four with psi);
- * alpha = <v, Hv> and beta = ||w|| reduced in double per block then summed on the
- * host in a fixed order; lowest eigenvalue of the tridiagonal matrix by Sturm-sequence
- * bisection in double.  Synchronous.
+ * tridiagonal eigenproblem are cheap).  Three device vectors of dtype (four with psi),
+ * or the caller's Krylov store with ED_REORTH_FULL; alpha = <v, Hv> and beta = ||w||
+ * reduced in double per block then summed on the host in a fixed order; the
+ * reorthogonalisation chosen by opts->reorth (default: a second sweep against the last
+ * two vectors), with alpha_j corrected by the sweeps' <v_j, w>; lowest eigenvalue of the
+ * tridiagonal matrix by Sturm-sequence bisection in double.  With psi and without a
+ * Krylov store the ground state comes from a second pass of the same recurrence
+ * (vectors recomputed, not stored).  Allocates a small sweep scratch (and the three
+ * vectors when work is NULL).  Synchronous.
  * Errors: ED_ERR_EMPTY (dim 0), ED_ERR_INVALID, ED_ERR_OOM, ED_ERR_CUDA.
  */
 int ed_lanczos(ed_basis *basis, const double *J, const double *Jz, const ed_lanczos_opts *opts,
@@ -290,7 +313,9 @@ int ed_batch_create(ed_basis *const *bases, int32_t n, const double *J, const do
  * pointers; x[s], y[s] hold dim_s * k elements of fp32 or complex fp32).  For k >= 2 every
  * non-empty sector's x[s] and y[s] must be 16-byte aligned, and x[s] 32-byte aligned when
  * a row holds 32 bytes or more (k = 8 real, k >= 4 complex): the kernel moves a row's k
- * entries with 16- and 32-byte accesses.  ED_ERR_INVALID otherwise.  Synchronous. */
+ * entries with 16- and 32-byte accesses.  ED_ERR_INVALID otherwise.  Synchronous: when an
+ * earlier ed_batch_apply may still run, the call first waits for it (the launch reads the
+ * sector table that this call rewrites). */
 int ed_batch_set_vectors(ed_batch *batch, void *const *x, void *const *y);
 
 /* ed_batch_apply -- y[s] = H_s x[s] for every sector, in one launch on stream.  The first call

@@ -22,6 +22,7 @@ __all__ = ["lib", "build", "build_basis", "build_basis_from", "Basis", "Batch", 
            "F64", "F32", "C128", "C64", "LIB_PATH", "SYMBOLS", "build_sectors", "dot_noalloc"]
 
 F64, F32, C128, C64 = 0, 1, 2, 3
+REORTH = {"local": 0, "none": 1, "full": 2}
 LIB_PATH = _build.LIB
 # every function declared in include/sced.h
 SYMBOLS = ["ed_build_basis", "ed_free_basis", "ed_basis_info", "ed_basis_export",
@@ -78,13 +79,16 @@ class _LOpts(ctypes.Structure):
                 ("v0", ctypes.c_void_p), ("psi", ctypes.c_void_p),
                 ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("work", ctypes.c_void_p),
-                ("work_bytes", ctypes.c_int64), ("tol_residual", ctypes.c_double)]
+                ("work_bytes", ctypes.c_int64), ("tol_residual", ctypes.c_double),
+                ("reorth", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("krylov", ctypes.c_void_p), ("krylov_bytes", ctypes.c_int64)]
 
 
 class _LRes(ctypes.Structure):
     _fields_ = [("E0", ctypes.c_double), ("steps", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("rq", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("ms_apply", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("ms_apply", ctypes.c_double),
+                ("ms_reorth", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -162,24 +166,45 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dev(t, dtype=None):
+def _need(*checks):
+    """Refuse, before any pointer is formed, every tensor whose element count is not the
+    expected one: checks are (tensor or None, expected count, name)."""
+    for t, n, what in checks:
+        if t is not None and t.numel() != n:
+            raise ValueError(f"{what} has {t.numel()} elements, expected {n}")
+
+
+def _dev(t, dtype=None, n=None, what="tensor", device=None):
+    """Device pointer of a contiguous CUDA tensor, after checking (in this order, so that
+    a wrong size is refused before anything else is looked at) its element count ``n``,
+    that it lives on CUDA device ``device`` (default: the current one), its layout and
+    its dtype.  Nothing reaches the library unless every check passes: a short vector
+    would let a kernel read or write past its end."""
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what} has {t.numel()} elements, expected {n}")
     if not t.is_cuda:
-        raise ValueError("expected a CUDA tensor")
+        raise ValueError(f"{what}: expected a CUDA tensor")
+    if device is None:
+        import torch
+        device = torch.cuda.current_device()
+    if t.device.index != device:
+        raise ValueError(f"{what} is on cuda:{t.device.index}, expected cuda:{device}")
     if not t.is_contiguous():
-        raise ValueError("expected a contiguous tensor")
+        raise ValueError(f"{what}: expected a contiguous tensor")
     if dtype is not None and t.dtype != dtype:
-        raise TypeError(f"expected {dtype}, got {t.dtype}")
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
     return ctypes.c_void_p(t.data_ptr())
 
 
 class Basis:
     """A symmetry sector's basis and lookup tables on the current CUDA device."""
 
-    def __init__(self, handle, J, Jz, n_classes):
+    def __init__(self, handle, J, Jz, n_classes, device=None):
         self._h = handle
         self.J = tuple(float(v) for v in J) if J is not None else None
         self.Jz = tuple(float(v) for v in Jz) if Jz is not None else None
         self.n_classes = n_classes
+        self.device = device      # CUDA device the basis was built on
         self._info = None
 
     def __del__(self):
@@ -237,41 +262,61 @@ class Basis:
         ph = torch.empty(n, dtype=torch.int32, device=dev)
         stab = torch.empty(n, dtype=torch.int32, device=dev)
         idx = torch.empty(n, dtype=torch.int64, device=dev)
-        _check(lib().ed_find_rep(self._h, _dev(states, torch.uint64), n, int(method), _dev(rep),
-                                 _dev(sym), _dev(ph), _dev(stab), _dev(idx), _stream(stream)))
+        d = self.device
+        _check(lib().ed_find_rep(self._h, _dev(states, torch.uint64, device=d, what="states"), n,
+                                 int(method), _dev(rep, device=d), _dev(sym, device=d),
+                                 _dev(ph, device=d), _dev(stab, device=d), _dev(idx, device=d),
+                                 _stream(stream)))
         return rep, sym, ph, stab, idx
 
     def apply_H(self, x, y=None, J=None, Jz=None, stream=None):
         """y = H x for CUDA tensors (float64/float32/complex128/complex64)."""
         import torch
+        D, d = self.dim, self.device
+        _need((x, D, "x"), (y, D, "y"))
+        px = _dev(x, n=D, what="x", device=d)
         if y is None:
             y = torch.empty_like(x)
+        py = _dev(y, x.dtype, n=D, what="y", device=d)
         cJ, cJz = self._couplings(J, Jz)
-        _check(lib().ed_apply_H(self._h, cJ, cJz, _dev(x), _dev(y, x.dtype), _dtype_code(x),
-                                _stream(stream)))
+        _check(lib().ed_apply_H(self._h, cJ, cJz, px, py, _dtype_code(x), _stream(stream)))
         return y
 
     def apply_H_rows(self, x, row_begin, row_end, y=None, J=None, Jz=None, stream=None):
         import torch
+        D, d = self.dim, self.device
+        if not 0 <= row_begin <= row_end <= D:
+            raise ValueError(f"rows [{row_begin}, {row_end}) outside [0, {D})")
+        _need((x, D, "x"), (y, row_end - row_begin, "y"))
+        px = _dev(x, n=D, what="x", device=d)
         if y is None:
             y = torch.empty(row_end - row_begin, dtype=x.dtype, device=x.device)
+        py = _dev(y, x.dtype, n=row_end - row_begin, what="y", device=d)
         cJ, cJz = self._couplings(J, Jz)
-        _check(lib().ed_apply_H_rows(self._h, cJ, cJz, _dev(x), _dev(y, x.dtype), _dtype_code(x),
+        _check(lib().ed_apply_H_rows(self._h, cJ, cJz, px, py, _dtype_code(x),
                                      int(row_begin), int(row_end), _stream(stream)))
         return y
 
     def apply_H_host(self, x, y=None, J=None, Jz=None, stream=None):
         """y = H x for HOST numpy arrays (or pinned CPU tensors); copies inside the call."""
+        D = self.dim
         if hasattr(x, "data_ptr"):
             import torch
             if y is None:
                 y = torch.empty_like(x)
+            for t, nm in ((x, "x"), (y, "y")):
+                if t.numel() != D or t.is_cuda or not t.is_contiguous():
+                    raise ValueError(f"{nm}: expected a contiguous host tensor of {D} elements")
+            if y.dtype != x.dtype:
+                raise TypeError("x and y differ in dtype")
             code = _dtype_code(x)
             px, py = ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())
         else:
             x = np.ascontiguousarray(x)
             if y is None:
                 y = np.empty_like(x)
+            if x.size != D or y.size != D or y.dtype != x.dtype or not y.flags.c_contiguous:
+                raise ValueError(f"x and y must be contiguous arrays of {D} elements of one dtype")
             code = _np_dtype_code(x)
             px, py = ctypes.c_void_p(x.ctypes.data), ctypes.c_void_p(y.ctypes.data)
         cJ, cJz = self._couplings(J, Jz)
@@ -286,45 +331,64 @@ class Basis:
 
     def expect_classes(self, x, Jz=None, stream=None):
         """Re <x|H_c|x> per coupling class c (unit exchange J_c = 1): numpy array."""
+        px = _dev(x, n=self.dim, what="x", device=self.device)
         _, cJz = self._couplings((1.0,) * self.n_classes, Jz)
         out = (ctypes.c_double * self.n_classes)()
-        _check(lib().ed_expect_classes(self._h, cJz, _dev(x), _dtype_code(x), out,
-                                       _stream(stream)))
+        _check(lib().ed_expect_classes(self._h, cJz, px, _dtype_code(x), out, _stream(stream)))
         return np.array(out[:])
 
     def dot(self, x, y, stream=None) -> complex:
+        D, d = self.dim, self.device
+        _need((x, D, "x"), (y, D, "y"))
+        px, py = _dev(x, n=D, what="x", device=d), _dev(y, x.dtype, n=D, what="y", device=d)
         out = (ctypes.c_double * 2)()
-        _check(lib().ed_dot(self._h, _dev(x), _dev(y, x.dtype), _dtype_code(x), out, _stream(stream)))
+        _check(lib().ed_dot(self._h, px, py, _dtype_code(x), out, _stream(stream)))
         return complex(out[0], out[1]) if x.is_complex() else out[0]
 
     def lanczos(self, J=None, Jz=None, dtype=None, max_steps=300, fixed_steps=0, tol=1e-13,
-                seed=1805, v0=None, psi=None, work=None, tol_residual=0.0, stream=None):
-        """Lanczos ground-state energy; returns a dict (E0, steps, converged, alpha, beta, ...)."""
+                seed=1805, v0=None, psi=None, work=None, tol_residual=0.0, reorth="local",
+                krylov=None, stream=None):
+        """Lanczos ground-state energy; returns a dict (E0, steps, converged, alpha, beta, ...).
+
+        reorth: "local" (default: a second Gram-Schmidt sweep against the last two
+        vectors), "none" (three-term recurrence only) or "full" (two sweeps against every
+        stored vector; ``krylov`` is a CUDA tensor of (steps + 1) * dim elements of dtype,
+        allocated here when None)."""
         import torch
         if dtype is None:
             dtype = torch.float64 if self.is_real else torch.complex128
         code = {torch.float64: F64, torch.float32: F32, torch.complex128: C128,
                 torch.complex64: C64}[dtype]
+        if reorth not in REORTH:
+            raise ValueError(f"reorth must be one of {sorted(REORTH)}")
         m = fixed_steps if fixed_steps > 0 else max_steps
+        if reorth == "full" and krylov is None:
+            krylov = torch.empty((m + 1) * self.dim, dtype=dtype, device=f"cuda:{self.device}")
         alpha = np.zeros(m)
         beta = np.zeros(m)
         o = _LOpts()
         o.max_steps, o.fixed_steps, o.tol, o.dtype, o.seed = int(max_steps), int(fixed_steps), float(tol), code, int(seed)
         o.tol_residual = float(tol_residual)
-        o.v0 = _dev(v0, dtype).value if v0 is not None else None
-        o.psi = _dev(psi, dtype).value if psi is not None else None
+        D, d = self.dim, self.device
+        _need((v0, D, "v0"), (psi, D, "psi"))
+        o.v0 = _dev(v0, dtype, n=D, what="v0", device=d).value if v0 is not None else None
+        o.psi = _dev(psi, dtype, n=D, what="psi", device=d).value if psi is not None else None
         o.alpha, o.beta = alpha.ctypes.data, beta.ctypes.data
         o.stream = _stream(stream).value
         if work is not None:
-            o.work = _dev(work).value
+            o.work = _dev(work, device=d, what="work").value
             o.work_bytes = work.numel() * work.element_size()
+        o.reorth = REORTH[reorth]
+        if krylov is not None:
+            o.krylov = _dev(krylov, dtype, device=d, what="krylov").value
+            o.krylov_bytes = krylov.numel() * krylov.element_size()
         r = _LRes()
         cJ, cJz = self._couplings(J, Jz)
         _check(lib().ed_lanczos(self._h, cJ, cJz, ctypes.byref(o), ctypes.byref(r)))
         k = r.steps
         return {"E0": r.E0, "steps": k, "converged": bool(r.converged), "rq": r.rq,
                 "alpha": alpha[:k].copy(), "beta": beta[:max(k - 1, 0)].copy(),
-                "ms_total": r.ms_total, "ms_apply": r.ms_apply}
+                "ms_total": r.ms_total, "ms_apply": r.ms_apply, "ms_reorth": r.ms_reorth}
 
 
 class Batch:
@@ -342,6 +406,17 @@ class Batch:
         self._h, self.k = h, int(k)
 
     def set_vectors(self, xs, ys):
+        import torch
+        if len(xs) != len(self.bases) or len(ys) != len(self.bases):
+            raise ValueError(f"need one x and one y per sector ({len(self.bases)})")
+        for s, (B, x, y) in enumerate(zip(self.bases, xs, ys)):
+            _need((x, B.dim * self.k, f"x[{s}]"), (y, B.dim * self.k, f"y[{s}]"))
+        for s, (B, x, y) in enumerate(zip(self.bases, xs, ys)):
+            n = B.dim * self.k
+            dt = torch.float32 if B.is_real else torch.complex64
+            if n:
+                _dev(x, dt, n=n, what=f"x[{s}]", device=B.device)
+                _dev(y, dt, n=n, what=f"y[{s}]", device=B.device)
         px = (ctypes.c_void_p * len(xs))(*[t.data_ptr() if t.numel() else None for t in xs])
         py = (ctypes.c_void_p * len(ys))(*[t.data_ptr() if t.numel() else None for t in ys])
         _check(lib().ed_batch_set_vectors(self._h, px, py))
@@ -375,8 +450,11 @@ def dot_noalloc(x, y, out, stream=None):
     import torch
     if out.dtype != torch.float64 or out.numel() < 2:
         raise TypeError("out must be a CUDA float64 tensor of 2 entries")
-    _check(lib().ed_dot_noalloc(_dev(x), _dev(y, x.dtype), x.numel(), _dtype_code(x), _dev(out),
-                                _stream(stream)))
+    n = x.numel()
+    _need((y, n, "y"))
+    py = _dev(y, x.dtype, n=n, what="y", device=x.device.index)
+    _check(lib().ed_dot_noalloc(_dev(x, what="x"), py, n, _dtype_code(x),
+                                _dev(out, what="out", device=x.device.index), _stream(stream)))
     return out
 
 
@@ -399,7 +477,8 @@ def build_basis(n_sites, n_sublat, bonds, bond_class, n_classes, perm, phase_num
     h = ctypes.c_void_p()
     _check(lib().ed_build_basis(ctypes.byref(L), ctypes.byref(G), ctypes.byref(R), int(n_up),
                                 ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
-    return Basis(h, J, Jz, int(n_classes))
+    import torch
+    return Basis(h, J, Jz, int(n_classes), device=torch.cuda.current_device())
 
 
 def build_basis_from(problem, **kw) -> Basis:

@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsced.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["capi.cu", "basis.cu", "apply.cu", "apply_fast.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "basis.cu", "apply.cu", "apply_fast.cu", "batch.cu", "noalloc.cu",
+           "reorth.cu"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -26,7 +26,7 @@ class _GroundStateEnergy(torch.autograd.Function):
         (J,) = ctx.saved_tensors
         B = ctx.basis
         dt = torch.float64 if B.is_real else torch.complex128
-        psi = torch.empty(B.dim, dtype=dt, device="cuda")
+        psi = torch.empty(B.dim, dtype=dt, device=f"cuda:{B.device}")
         kw = dict(ctx.kw)
         kw["dtype"] = dt
         kw.setdefault("tol_residual", 1e-10)   # dE0/dJ is first order in the state's error

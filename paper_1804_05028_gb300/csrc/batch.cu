@@ -49,6 +49,7 @@ struct ed_batch {
   int sm_count = 0;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t graph_stream = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after every launch: set_vectors waits on it
   bool vectors_set = false;
 };
 
@@ -404,6 +405,9 @@ extern "C" int ed_batch_set_vectors(ed_batch *Bt, void *const *x, void *const *y
   }
   Bt->vectors_set = true;
   if (Bt->rows_per_item) {   // the kernel reads the sector table from device memory
+    // a launch still in flight on the caller's stream reads that table: let it finish
+    // before overwriting it (a pageable copy is not ordered against other streams)
+    if (Bt->done) ED_CK(cudaEventSynchronize(Bt->done));
     ED_CK(cudaMemcpy(Bt->d_sec, Bt->host.data(), sizeof(BatchSector) * Bt->n, cudaMemcpyHostToDevice));
   }
   return ED_OK;
@@ -417,25 +421,29 @@ extern "C" int ed_batch_apply(ed_batch *Bt, void *stream) {
   if (!Bt->rows_per_item) {
     // pick the tile: time each candidate (second of two runs) and keep the fastest
     const int cand[] = {32, 64, 128, 256};   // rows per work item of one warp
-    cudaEvent_t e0, e1;
-    ED_CK(cudaEventCreate(&e0));
-    ED_CK(cudaEventCreate(&e1));
+    struct Events {   // destroyed on every exit path
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      ~Events() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+      }
+    } ev;
+    ED_CK(cudaEventCreate(&ev.e0));
+    ED_CK(cudaEventCreate(&ev.e1));
     float best = 1e30f;
     int pick = 256;
     for (int c : cand) {
       float ms = 0;
       if ((rc = upload(Bt, c))) return rc;
       for (int rep = 0; rep < 2; rep++) {
-        ED_CK(cudaEventRecord(e0, st));
+        ED_CK(cudaEventRecord(ev.e0, st));
         if ((rc = launch(Bt, c, st))) return rc;
-        ED_CK(cudaEventRecord(e1, st));
-        ED_CK(cudaEventSynchronize(e1));
-        ED_CK(cudaEventElapsedTime(&ms, e0, e1));
+        ED_CK(cudaEventRecord(ev.e1, st));
+        ED_CK(cudaEventSynchronize(ev.e1));
+        ED_CK(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
       }
       if (ms < best) { best = ms; pick = c; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     Bt->rows_per_item = pick;
     if ((rc = upload(Bt, pick))) return rc;
   }
@@ -455,7 +463,9 @@ extern "C" int ed_batch_apply(ed_batch *Bt, void *stream) {
     cudaStreamDestroy(cs);
     if (ie != cudaSuccess) return ed_cuda_fail(ie, "cudaGraphInstantiate");
   }
+  if (!Bt->done) ED_CK(cudaEventCreateWithFlags(&Bt->done, cudaEventDisableTiming));
   ED_CK(cudaGraphLaunch(Bt->exec, st));
+  ED_CK(cudaEventRecord(Bt->done, st));
   return ED_OK;
 }
 
@@ -468,6 +478,10 @@ extern "C" int ed_batch_info(const ed_batch *Bt, int32_t *rows_per_item, int64_t
 
 extern "C" void ed_batch_free(ed_batch *Bt) {
   if (!Bt) return;
+  if (Bt->done) {
+    cudaEventSynchronize(Bt->done);
+    cudaEventDestroy(Bt->done);
+  }
   if (Bt->exec) cudaGraphExecDestroy(Bt->exec);
   if (Bt->d_sec) cudaFree(Bt->d_sec);
   if (Bt->d_item0) cudaFree(Bt->d_item0);

@@ -646,17 +646,27 @@ extern "C" int ed_apply_H_host(ed_basis *B, const double *J, const double *Jz, c
   }
   const size_t es = elem_size(dtype);
   ED_CK(cudaMemcpyAsync(B->d_stage_x, xh, bytes, cudaMemcpyHostToDevice, st));
+  // on an error after some chunks were queued, their copies into the caller's y are
+  // drained before the call returns
+  auto drain = [&](int code) {
+    if (n_chunks > 1) cudaStreamSynchronize(B->copy_stream);
+    cudaStreamSynchronize(st);
+    return code;
+  };
   for (int c = 0; c < n_chunks; c++) {
     const int64_t r0 = B->D * c / n_chunks, r1 = B->D * (c + 1) / n_chunks;
     char *yd = (char *)B->d_stage_y + (size_t)r0 * es;
-    if ((rc = ed_launch_apply(B, J, Jz, B->d_stage_x, yd, dtype, r0, r1, nullptr, st))) return rc;
+    if ((rc = ed_launch_apply(B, J, Jz, B->d_stage_x, yd, dtype, r0, r1, nullptr, st))) return drain(rc);
+    cudaError_t e;
     if (n_chunks == 1) {
-      ED_CK(cudaMemcpyAsync(yh, B->d_stage_y, bytes, cudaMemcpyDeviceToHost, st));
+      e = cudaMemcpyAsync(yh, B->d_stage_y, bytes, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return drain(ed_cuda_fail(e, "cudaMemcpyAsync"));
     } else {
-      ED_CK(cudaEventRecord(B->chunk_done[c], st));
-      ED_CK(cudaStreamWaitEvent(B->copy_stream, B->chunk_done[c], 0));
-      ED_CK(cudaMemcpyAsync((char *)yh + (size_t)r0 * es, yd, (size_t)(r1 - r0) * es,
-                            cudaMemcpyDeviceToHost, B->copy_stream));
+      if ((e = cudaEventRecord(B->chunk_done[c], st)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(B->copy_stream, B->chunk_done[c], 0)) != cudaSuccess ||
+          (e = cudaMemcpyAsync((char *)yh + (size_t)r0 * es, yd, (size_t)(r1 - r0) * es,
+                               cudaMemcpyDeviceToHost, B->copy_stream)) != cudaSuccess)
+        return drain(ed_cuda_fail(e, "chunked copy of y"));
     }
   }
   if (n_chunks > 1) ED_CK(cudaStreamSynchronize(B->copy_stream));
@@ -733,18 +743,77 @@ struct LanczosRun {
   int dtype;
   bool cplx;
   cudaStream_t st;
-  void *v[3];        // rotating: vprev, v, w
-  cudaEvent_t e0, e1;
-  double ms_apply = 0;
+  void *v[3];        // rotating: vprev, v, w (local or no reorthogonalisation)
+  char *store = nullptr;   // full reorthogonalisation: slot k holds v_k
+  int store_slots = 0;
+  int reorth = ED_REORTH_LOCAL;
+  double *d_ro = nullptr;  // sweep partials [m_cap * P * grid], then coefficients [m_cap * P]
+  size_t ro_coef_off = 0;
+  cudaEvent_t e0, e1, r0, r1;
+  double ms_apply = 0, ms_reorth = 0;
+  void *slot(int k) const { return store + (size_t)k * elem_bytes(); }
+  size_t elem_bytes() const {
+    return (dtype == ED_F64 ? 8 : dtype == ED_F32 ? 4 : dtype == ED_C128 ? 16 : 8) * (size_t)B->D;
+  }
 };
 
-// one Lanczos pass; when coef != null, also accumulates psi += coef[j] v_j
+// The sweeps of step j after the three-term update of w.  Local: one sweep against v_j and
+// v_{j-1} (the second Gram-Schmidt pass of the recurrence's own projection).  Full: two
+// sweeps against every stored v_0 .. v_j (classical Gram-Schmidt, twice).  *corr gets
+// Re <v_j, w> summed over the sweeps (added to alpha_j so that the tridiagonal matrix stays
+// the projection of H), *b2 the new ||w||^2; both only when want_host (the replay pass
+// reuses the stored alpha and beta and skips the copies).
+int reorth_step(LanczosRun &L, int j, void *w, const void *v, const void *vprev, bool want_host,
+                double *corr, double *b2) {
+  ed_basis *B = L.B;
+  const int P = L.cplx ? 2 : 1;
+  const int grid = ed_reorth_grid(B);
+  double *c = L.d_ro + L.ro_coef_off;
+  ED_CK(cudaEventRecord(L.r0, L.st));
+  const int sweeps = L.reorth == ED_REORTH_FULL ? 2 : 1;
+  double cj = 0.0;
+  for (int sw = 0; sw < sweeps; sw++) {
+    int rc, jj;
+    if (L.reorth == ED_REORTH_FULL) {
+      rc = ed_launch_reorth_sweep(B, w, L.store, nullptr, nullptr, j + 1, L.dtype, L.d_ro, c, L.st);
+      jj = j;
+    } else {
+      rc = ed_launch_reorth_sweep(B, w, nullptr, v, vprev, j ? 2 : 1, L.dtype, L.d_ro, c, L.st);
+      jj = 0;
+    }
+    if (rc) return rc;
+    if (want_host) {
+      double h = 0;
+      ED_CK(cudaMemcpyAsync(&B->h_partial[0], c + (size_t)jj * P, 8, cudaMemcpyDeviceToHost, L.st));
+      ED_CK(cudaStreamSynchronize(L.st));
+      h = B->h_partial[0];
+      cj += h;
+    }
+  }
+  ED_CK(cudaEventRecord(L.r1, L.st));
+  if (want_host) {
+    double nn = 0, im = 0;
+    int rc = reduce_partials(B, L.d_ro, grid, false, L.st, &nn, &im);
+    if (rc) return rc;
+    float ms = 0;
+    ED_CK(cudaEventElapsedTime(&ms, L.r0, L.r1));
+    L.ms_reorth += ms;
+    *corr = cj;
+    *b2 = nn;
+  }
+  return ED_OK;
+}
+
+// one Lanczos pass; when coef != null, also accumulates psi += coef[j] v_j (replay of the
+// first pass from its stored alpha / beta: same operations, so the same vectors)
 int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fixed, double tol,
-                 std::vector<double> &alpha, std::vector<double> &beta, double *E0, int *steps,
-                 int *converged, const std::vector<double> *coef, void *psi) {
+                 std::vector<double> &alpha, std::vector<double> &alpha_rec,
+                 std::vector<double> &beta, double *E0, int *steps, int *converged,
+                 const std::vector<double> *coef, void *psi) {
   ed_basis *B = L.B;
   const int nblk = B->n_partial / 2;
-  void *vprev = L.v[0], *v = L.v[1], *w = L.v[2];
+  const bool full = L.reorth == ED_REORTH_FULL;
+  void *vprev = full ? nullptr : L.v[0], *v = full ? L.slot(0) : L.v[1], *w = full ? nullptr : L.v[2];
   int rc;
   // start vector, normalised
   if (o->v0) { if ((rc = ed_launch_copy(B, v, o->v0, L.dtype, L.st))) return rc; }
@@ -763,6 +832,7 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
   bool have_old = false;
   *converged = 0;
   for (int j = 0; j < m_total; j++) {
+    if (full) { v = L.slot(j); vprev = j ? L.slot(j - 1) : nullptr; w = L.slot(j + 1); }
     if (replay) { if ((rc = ed_launch_axpy(B, psi, v, (*coef)[j], L.dtype, L.st))) return rc; }
     if (replay && j == m_total - 1) break;
     ED_CK(cudaEventRecord(L.e0, L.st));
@@ -770,7 +840,7 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
     ED_CK(cudaEventRecord(L.e1, L.st));
     double a;
     if (replay) {
-      a = alpha[j];
+      a = alpha_rec[j];
     } else {
       if ((rc = reduce_partials(B, B->d_partial, B->last_apply_grid, L.cplx, L.st, &a, nullptr))) return rc;
     }
@@ -780,11 +850,16 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
     L.ms_apply += ms;
     const double bprev = j ? beta[j - 1] : 0.0;
     if ((rc = ed_launch_axpy_norm(B, w, v, j ? vprev : nullptr, a, bprev, L.dtype, B->d_partial, nblk, L.st))) return rc;
-    double b2;
-    if ((rc = reduce_partials(B, B->d_partial, nblk, false, L.st, &b2, nullptr))) return rc;
+    double b2 = 0, corr = 0;
+    if (L.reorth != ED_REORTH_NONE) {
+      if ((rc = reorth_step(L, j, w, v, j ? vprev : nullptr, !replay, &corr, &b2))) return rc;
+    } else if (!replay) {
+      if ((rc = reduce_partials(B, B->d_partial, nblk, false, L.st, &b2, nullptr))) return rc;
+    }
     double b = replay ? beta[j] : std::sqrt(std::max(b2, 0.0));
     if (!replay) {
-      alpha.push_back(a);
+      alpha_rec.push_back(a);
+      alpha.push_back(a + corr);
       const double e = lowest_eigenvalue(alpha, beta, (int)alpha.size());
       *E0 = e;
       *steps = j + 1;
@@ -810,7 +885,7 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
       beta.push_back(b);
     }
     if ((rc = ed_launch_scale(B, w, 1.0 / b, L.dtype, L.st))) return rc;
-    void *t = vprev; vprev = v; v = w; w = t;
+    if (!full) { void *t = vprev; vprev = v; v = w; w = t; }
   }
   return ED_OK;
 }
@@ -826,18 +901,33 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
   if (B->D == 0) return ed_fail(ED_ERR_EMPTY, "sector has dimension 0");
   int rc = check_dtype(B, o.dtype);
   if (rc) return rc;
-  const int max_steps = o.fixed_steps > 0 ? o.fixed_steps : (o.max_steps > 0 ? o.max_steps : 300);
+  if (o.reorth != ED_REORTH_LOCAL && o.reorth != ED_REORTH_NONE && o.reorth != ED_REORTH_FULL)
+    return ed_fail(ED_ERR_INVALID, "reorth must be ED_REORTH_LOCAL, ED_REORTH_NONE or ED_REORTH_FULL");
+  int max_steps = o.fixed_steps > 0 ? o.fixed_steps : (o.max_steps > 0 ? o.max_steps : 300);
   const double tol = o.tol > 0 ? o.tol : 1e-13;
   auto t0 = std::chrono::steady_clock::now();
   LanczosRun L{};
   L.B = B; L.J = J; L.Jz = Jz; L.dtype = o.dtype;
   L.cplx = o.dtype == ED_C128 || o.dtype == ED_C64;
   L.st = (cudaStream_t)o.stream;
+  L.reorth = o.reorth;
   const size_t bytes = elem_size(o.dtype) * (size_t)B->D;
-  const bool own = o.work == nullptr;
-  if (!own && o.work_bytes < (int64_t)(3 * bytes))
+  const bool full = o.reorth == ED_REORTH_FULL;
+  const bool own = !full && o.work == nullptr;
+  if (full) {
+    if (!o.krylov) return ed_fail(ED_ERR_INVALID, "ED_REORTH_FULL needs a Krylov store");
+    const int64_t slots = o.krylov_bytes / (int64_t)bytes;
+    if (slots < 2) return ed_fail(ED_ERR_INVALID, "Krylov store smaller than 2 vectors");
+    L.store = (char *)o.krylov;
+    L.store_slots = (int)std::min<int64_t>(slots, 100000);
+    // step j writes w into slot j + 1; the sweeps' shared memory bounds the store too
+    max_steps = std::min(max_steps, std::min(L.store_slots - 1, 1024));
+    if (o.fixed_steps > 0 && o.fixed_steps > max_steps)
+      return ed_fail(ED_ERR_INVALID, "Krylov store too small for fixed_steps");
+  } else if (!own && o.work_bytes < (int64_t)(3 * bytes)) {
     return ed_fail(ED_ERR_INVALID, "Lanczos workspace smaller than 3 vectors");
-  for (int k = 0; k < 3; k++) {
+  }
+  for (int k = 0; k < 3 && !full; k++) {
     if (!own) { L.v[k] = (char *)o.work + k * bytes; continue; }
     if (cudaMalloc(&L.v[k], bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -845,29 +935,51 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
       return ed_fail(ED_ERR_OOM, "cannot allocate Lanczos vectors");
     }
   }
+  // sweep scratch: partials of up to m_cap vectors per block, then their coefficients
+  const int m_cap = full ? max_steps + 1 : 2;
+  const int P = L.cplx ? 2 : 1;
+  L.ro_coef_off = (size_t)m_cap * P * ed_reorth_grid(B);
+  if (o.reorth != ED_REORTH_NONE &&
+      cudaMalloc(&L.d_ro, sizeof(double) * (L.ro_coef_off + (size_t)m_cap * P)) != cudaSuccess) {
+    cudaGetLastError();
+    if (own) for (int k = 0; k < 3; k++) cudaFree(L.v[k]);
+    return ed_fail(ED_ERR_OOM, "cannot allocate the reorthogonalisation scratch");
+  }
   ED_CK(cudaEventCreate(&L.e0));
   ED_CK(cudaEventCreate(&L.e1));
-  std::vector<double> alpha, beta;
+  ED_CK(cudaEventCreate(&L.r0));
+  ED_CK(cudaEventCreate(&L.r1));
+  std::vector<double> alpha, alpha_rec, beta;
   double E0 = 0;
   int steps = 0, conv = 0;
-  rc = lanczos_pass(L, &o, max_steps, o.fixed_steps > 0, tol, alpha, beta, &E0, &steps, &conv,
-                    nullptr, nullptr);
+  rc = lanczos_pass(L, &o, max_steps, o.fixed_steps > 0, tol, alpha, alpha_rec, beta, &E0, &steps,
+                    &conv, nullptr, nullptr);
   if (!rc && o.psi) {
     const int m = (int)alpha.size();
     std::vector<double> bt(beta.begin(), beta.begin() + std::max(0, m - 1));
     std::vector<double> s = tri_eigvec(alpha, bt, m, E0);
-    std::vector<double> a2 = alpha, b2 = bt;
-    double e_dummy;
-    int st_dummy, cv_dummy;
-    rc = lanczos_pass(L, &o, m, true, tol, a2, b2, &e_dummy, &st_dummy, &cv_dummy, &s, o.psi);
+    if (full) {   // the Krylov basis is stored: psi = sum_k s_k v_k, no second pass
+      double *d_s = L.d_ro;   // the sweep partials are free again
+      rc = ED_OK;
+      if (cudaMemcpyAsync(d_s, s.data(), sizeof(double) * m, cudaMemcpyHostToDevice, L.st) != cudaSuccess)
+        rc = ed_fail(ED_ERR_CUDA, "copy of the Ritz coefficients");
+      if (!rc) rc = ed_launch_combine(B, o.psi, L.store, m, d_s, o.dtype, L.st);
+      if (!rc && cudaStreamSynchronize(L.st) != cudaSuccess) rc = ed_fail(ED_ERR_CUDA, "combine");
+    } else {
+      std::vector<double> a2 = alpha, ar2 = alpha_rec, b2 = bt;
+      double e_dummy;
+      int st_dummy, cv_dummy;
+      rc = lanczos_pass(L, &o, m, true, tol, a2, ar2, b2, &e_dummy, &st_dummy, &cv_dummy, &s, o.psi);
+    }
     if (!rc) {
       // normalise psi and take its Rayleigh quotient
       double nn, im;
       const int nblk = B->n_partial / 2;
+      void *scratch = full ? L.slot(std::min(m, L.store_slots - 1)) : L.v[0];
       rc = ed_launch_dot(B, o.psi, o.psi, o.dtype, B->d_partial, nblk, L.st);
       if (!rc) rc = reduce_partials(B, B->d_partial, nblk, L.cplx, L.st, &nn, &im);
       if (!rc) rc = ed_launch_scale(B, o.psi, 1.0 / std::sqrt(nn), o.dtype, L.st);
-      if (!rc) rc = ed_launch_apply(B, J, Jz, o.psi, L.v[0], o.dtype, 0, B->D, B->d_partial, L.st);
+      if (!rc) rc = ed_launch_apply(B, J, Jz, o.psi, scratch, o.dtype, 0, B->D, B->d_partial, L.st);
       double rq = 0;
       if (!rc) rc = reduce_partials(B, B->d_partial, B->last_apply_grid, L.cplx, L.st, &rq, nullptr);
       res->rq = rq;
@@ -878,12 +990,17 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
     res->steps = steps;
     res->converged = conv;
     res->ms_apply = L.ms_apply;
+    res->ms_reorth = L.ms_reorth;
     if (o.alpha) for (size_t k = 0; k < alpha.size(); k++) o.alpha[k] = alpha[k];
     if (o.beta) for (size_t k = 0; k < beta.size(); k++) o.beta[k] = beta[k];
   }
+  cudaStreamSynchronize(L.st);
   if (own) for (int k = 0; k < 3; k++) cudaFree(L.v[k]);
+  if (L.d_ro) cudaFree(L.d_ro);
   cudaEventDestroy(L.e0);
   cudaEventDestroy(L.e1);
+  cudaEventDestroy(L.r0);
+  cudaEventDestroy(L.r1);
   res->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return rc;
 }

@@ -353,3 +353,11 @@ struct ed_batch;
 extern "C" void ed_batch_free(ed_batch *batch);
 int ed_launch_count(const ed_basis *B, unsigned long long *d_out, cudaStream_t st);
 int ed_launch_copy(const ed_basis *B, void *dst, const void *src, int dtype, cudaStream_t st);
+// reorth.cu: one Gram-Schmidt sweep of w against m vectors (base + k * D, or p0 / p1),
+// coefficients into c (m, or 2m for complex), ||w||^2 block partials into partial[0, grid)
+int ed_reorth_grid(const ed_basis *B);
+int ed_launch_reorth_sweep(const ed_basis *B, void *w, const void *base, const void *p0,
+                           const void *p1, int m, int dtype, double *partial, double *c,
+                           cudaStream_t st);
+int ed_launch_combine(const ed_basis *B, void *psi, const void *base, int m, const double *s,
+                      int dtype, cudaStream_t st);

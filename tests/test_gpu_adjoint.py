@@ -76,19 +76,30 @@ def test_dE0_dJ_autograd_fd_and_hellmann_feynman(J2):
     assert abs(E.item() - ev[0]) < 1e-10 * abs(ev[0])
 
 
-def test_dE0_dJ_square36_j2_half():
-    """Full 6x6 J1-J2 Gamma-A1 sector at J2 = 0.5: autograd against central differences."""
+@pytest.fixture(scope="module")
+def square36():
+    B = _ed().build_basis_from(w.config_square36(0.5))
+    yield B
+    B.close()
+
+
+@pytest.mark.parametrize("J2", [0.40, 0.45, 0.50, 0.55, 0.60])
+def test_dE0_dJ_square36_scan(square36, J2):
+    """Full 6x6 J1-J2 Gamma-A1 sector (the basis does not depend on the couplings), J2 in
+    {0.40, ..., 0.60}: autograd against central differences (h = 1e-4, fp64) for both
+    couplings, and Euler's identity sum_c J_c dE0/dJ_c = E0 (E0 is homogeneous of degree
+    one in J)."""
     from paper_1804_05028_gb300.autograd import ground_state_energy
-    p = w.config_square36(0.5)
-    B = _ed().build_basis_from(p)
-    J = torch.tensor([1.0, 0.5], dtype=torch.float64, requires_grad=True)
+    B = square36
+    J = torch.tensor([1.0, J2], dtype=torch.float64, requires_grad=True)
     E = ground_state_energy(B, J)
     E.backward()
     g = J.grad.numpy()
     h = 1e-4
-    Jp = [1.0, 0.5 + h]
-    Jm = [1.0, 0.5 - h]
-    fd2 = (B.lanczos(J=Jp)["E0"] - B.lanczos(J=Jm)["E0"]) / (2 * h)
-    assert abs(g[1] - fd2) < 2e-6
-    # Euler: E0 is homogeneous of degree 1 in J, so sum_c J_c dE0/dJ_c = E0
-    assert abs(1.0 * g[0] + 0.5 * g[1] - E.item()) < 1e-8 * abs(E.item())
+    for c in range(2):
+        Jp, Jm = [1.0, J2], [1.0, J2]
+        Jp[c] += h
+        Jm[c] -= h
+        fd = (B.lanczos(J=Jp)["E0"] - B.lanczos(J=Jm)["E0"]) / (2 * h)
+        assert abs(g[c] - fd) < 2e-6, (c, g[c], fd)
+    assert abs(1.0 * g[0] + J2 * g[1] - E.item()) < 1e-8 * abs(E.item())

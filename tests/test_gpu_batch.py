@@ -4,7 +4,8 @@ with block vectors k = 1, 4, 8 (fp32 / complex fp32).
 
 Pins: every sector's dimension against the character-projection count; three sectors
 bit-exact against the oracle's basis; sampled rows against the oracle's matrix-free
-rows; every column of every batched product against the single-sector product."""
+rows; every column of every batched product against the single-sector product, and on
+four sectors against the oracle's stored matrix."""
 import numpy as np
 import pytest
 
@@ -146,4 +147,75 @@ def test_batched_sublattice_sectors(k):
     X = xs[3].view(bases[3].dim, k).cpu().numpy().astype(np.complex128)
     Y = ys[3].view(bases[3].dim, k).cpu().numpy()
     assert np.abs(Y - H @ X).max() <= 2e-6 * np.abs(H @ X).max()
+    bt.close()
+
+
+def test_whole_table_batch_against_oracle(sectors):
+    """The whole-table batched kernel (the variant the 572-sector launch runs) against the
+    oracle's stored matrix directly, every column of every block width, on four sectors:
+    real Gamma with the full C4v little group, a complex momentum, a mirror little group,
+    and the largest sector of the set."""
+    import paper_1804_05028_gb300 as ed
+    probs, bases = sectors
+    largest = int(np.argmax([B.dim for B in bases]))
+    picks = [
+        _pick(probs, lambda p: p.n_up == 14 and p.is_real() and p.n_sym == 200),
+        _pick(probs, lambda p: p.n_up == 14 and not p.is_real()),
+        _pick(probs, lambda p: p.n_up == 13 and p.n_sym == 50),
+        largest,
+    ]
+    assert len(set(picks)) == 4 and bases[largest].dim > 200000
+    refs = {}
+    for i in picks:
+        refs[i] = oracle.stored_matrix(probs[i])
+    for k in (1, 4, 8):
+        g = torch.Generator(device="cuda").manual_seed(1804 + k)
+        xs = [torch.randn(B.dim * k, dtype=torch.float32 if B.is_real else torch.complex64,
+                          device="cuda", generator=g) for B in bases]
+        ys = [torch.full_like(x, float("nan")) for x in xs]
+        bt = ed.Batch(bases, k=k)
+        bt.set_vectors(xs, ys)
+        bt.apply()
+        torch.cuda.synchronize()
+        for i in picks:
+            B = bases[i]
+            X = xs[i].view(B.dim, k).cpu().numpy()
+            Y = ys[i].view(B.dim, k).cpu().numpy()
+            for v in range(k):
+                xv = X[:, v].astype(np.complex128 if not B.is_real else np.float64)
+                ref = refs[i].matvec(xv)
+                err = np.abs(Y[:, v] - ref).max()
+                assert err <= 2e-6 * np.abs(ref).max(), (probs[i].name, k, v, err)
+        bt.close()
+
+
+def test_set_vectors_between_applies_on_a_stream(sectors):
+    """Vectors swapped between two launches queued on a non-blocking stream: the first
+    launch still computes with the first vectors (set_vectors waits for it before it
+    rewrites the sector table the launch reads)."""
+    import paper_1804_05028_gb300 as ed
+    probs, bases = sectors
+    sub = [B for B in bases if B.dim][:40]
+    g = torch.Generator(device="cuda").manual_seed(5)
+    mk = lambda: [torch.randn(B.dim, dtype=torch.float32 if B.is_real else torch.complex64,
+                              device="cuda", generator=g) for B in sub]
+    xa, xb = mk(), mk()
+    ya = [torch.full_like(x, float("nan")) for x in xa]
+    yb = [torch.full_like(x, float("nan")) for x in xb]
+    bt = ed.Batch(sub, k=1)
+    bt.set_vectors(xa, ya)
+    bt.apply()                     # tunes and captures (synchronous)
+    st = torch.cuda.Stream()
+    for _ in range(3):
+        for y in ya + yb:
+            y.fill_(float("nan"))
+        torch.cuda.synchronize()
+        bt.set_vectors(xa, ya)
+        bt.apply(stream=st)
+        bt.set_vectors(xb, yb)
+        bt.apply(stream=st)
+        st.synchronize()
+        for B, x1, y1, x2, y2 in zip(sub, xa, ya, xb, yb):
+            assert torch.allclose(y1, B.apply_H(x1), rtol=0, atol=2e-6 * max(1.0, y1.abs().max().item()))
+            assert torch.allclose(y2, B.apply_H(x2), rtol=0, atol=2e-6 * max(1.0, y2.abs().max().item()))
     bt.close()
