@@ -349,6 +349,27 @@ void ed_batch_free(ed_batch *batch);
 int ed_dot_noalloc(const void *x, const void *y, int64_t n, int32_t dtype, double *out,
                    void *stream);
 
+/*
+ * Vector operations on a slice of a Lanczos vector (Sec. IV: the product dominates the
+ * Lanczos iteration; scalings, updates and dot products are streaming passes).  They let a
+ * driver that holds only part of every vector -- e.g. one rank of a row-sharded Lanczos --
+ * run its rank-local arithmetic in the library; ed_lanczos needs none of them.  fp32
+ * vectors are updated and summed in double-float arithmetic (pairs of fp32 words, exact
+ * fp32 products), fp64 vectors in fp64; every reduction has a fixed order.  All pointers
+ * are DEVICE pointers on the current device, caller-owned; asynchronous on stream.
+ */
+
+/* ed_axpy_norm -- w <- w - a v - b vprev over n elements of dtype (vprev may be NULL; a and
+ * b real, as in the Hermitian tridiagonal recurrence), then norm2[0] = ||w||^2 in double.
+ * scratch: DEVICE array of scratch_len >= 1 doubles for block partials (more blocks are used
+ * when it is longer, up to 4 per SM).  Errors: ED_ERR_INVALID (negative n, null pointers,
+ * unknown dtype), ED_ERR_CUDA. */
+int ed_axpy_norm(void *w, const void *v, const void *vprev, double a, double b, int64_t n,
+                 int32_t dtype, double *scratch, int64_t scratch_len, double *norm2, void *stream);
+
+/* ed_scale -- x <- s x over n elements of dtype.  Errors: ED_ERR_INVALID, ED_ERR_CUDA. */
+int ed_scale(void *x, double s, int64_t n, int32_t dtype, void *stream);
+
 /* ed_last_error -- message of the last failing call on this thread ("" if none). */
 const char *ed_last_error(void);
 

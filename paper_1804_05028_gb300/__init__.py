@@ -19,7 +19,8 @@ import numpy as np
 from . import _build
 
 __all__ = ["lib", "build", "build_basis", "build_basis_from", "Basis", "Batch", "EdError",
-           "F64", "F32", "C128", "C64", "LIB_PATH", "SYMBOLS", "build_sectors", "dot_noalloc"]
+           "F64", "F32", "C128", "C64", "LIB_PATH", "SYMBOLS", "build_sectors", "dot_noalloc",
+           "axpy_norm", "scale"]
 
 F64, F32, C128, C64 = 0, 1, 2, 3
 REORTH = {"local": 0, "none": 1, "full": 2}
@@ -29,7 +30,7 @@ SYMBOLS = ["ed_build_basis", "ed_free_basis", "ed_basis_info", "ed_basis_export"
            "ed_find_rep", "ed_apply_H", "ed_apply_H_rows", "ed_apply_H_host", "ed_lanczos",
            "ed_dot", "ed_count_terms", "ed_expect_classes", "ed_dot_noalloc", "ed_batch_create",
            "ed_batch_set_vectors", "ed_batch_apply", "ed_batch_info", "ed_batch_free",
-           "ed_last_error", "ed_version"]
+           "ed_axpy_norm", "ed_scale", "ed_last_error", "ed_version"]
 
 _ERR = {1: "ED_ERR_INVALID", 2: "ED_ERR_UNSTABLE", 3: "ED_ERR_OOM", 4: "ED_ERR_CUDA",
         5: "ED_ERR_TIMEOUT", 6: "ED_ERR_EMPTY", 7: "ED_ERR_UNSUPPORTED"}
@@ -130,6 +131,9 @@ def lib():
             L.ed_batch_info.argtypes = [vp, vp, vp]
             L.ed_batch_free.argtypes = [vp]
             L.ed_batch_free.restype = None
+            L.ed_axpy_norm.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, i64, i32, vp,
+                                       i64, vp, vp]
+            L.ed_scale.argtypes = [vp, ctypes.c_double, i64, i32, vp]
             L.ed_last_error.restype = ctypes.c_char_p
             L.ed_version.restype = ctypes.c_char_p
             _lib = L
@@ -456,6 +460,31 @@ def dot_noalloc(x, y, out, stream=None):
     _check(lib().ed_dot_noalloc(_dev(x, what="x"), py, n, _dtype_code(x),
                                 _dev(out, what="out", device=x.device.index), _stream(stream)))
     return out
+
+
+def axpy_norm(w, v, vprev, a, b, scratch, norm2, stream=None):
+    """ed_axpy_norm: w <- w - a v - b vprev in place (vprev may be None), ||w||^2 into the
+    CUDA float64 tensor ``norm2`` (1 entry), block partials in the CUDA float64 tensor
+    ``scratch``.  Asynchronous."""
+    import torch
+    n = w.numel()
+    _need((v, n, "v"), (vprev, n, "vprev"))
+    if scratch.dtype != torch.float64 or norm2.dtype != torch.float64 or norm2.numel() < 1:
+        raise TypeError("scratch and norm2 must be CUDA float64 tensors")
+    d = w.device.index
+    pw = _dev(w, what="w", device=d)
+    pv = _dev(v, w.dtype, what="v", device=d)
+    pp = _dev(vprev, w.dtype, what="vprev", device=d) if vprev is not None else None
+    _check(lib().ed_axpy_norm(pw, pv, pp, float(a), float(b), n, _dtype_code(w),
+                              _dev(scratch, what="scratch", device=d), scratch.numel(),
+                              _dev(norm2, what="norm2", device=d), _stream(stream)))
+    return norm2
+
+
+def scale(x, s, stream=None):
+    """ed_scale: x <- s x in place for a CUDA tensor.  Asynchronous."""
+    _check(lib().ed_scale(_dev(x, what="x"), float(s), x.numel(), _dtype_code(x), _stream(stream)))
+    return x
 
 
 def build_basis(n_sites, n_sublat, bonds, bond_class, n_classes, perm, phase_num, phase_denom,

@@ -12,7 +12,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsced.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["capi.cu", "basis.cu", "apply.cu", "apply_fast.cu", "batch.cu", "noalloc.cu",
-           "reorth.cu"]
+           "reorth.cu", "vector.cu"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

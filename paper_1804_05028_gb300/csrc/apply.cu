@@ -9,6 +9,7 @@
 // of the push of Alg. 4, exact because H is Hermitian.  Each y_i is written once:
 // no atomics, no inter-block communication, fixed summation order.
 #include "sced_internal.cuh"
+#include "dfloat.cuh"
 #include <cstdlib>
 
 namespace {
@@ -263,16 +264,46 @@ __global__ void dot_kernel(const V *x, const V *y, int64_t n, double *partial) {
   if (Vt<V>::cplx) block_reduce_store<double>(im, partial, gridDim.x + blockIdx.x);
 }
 
-// w <- w - a v - b vprev ; partial ||w||^2   (vprev may be null)
+// w <- w - a v - b vprev ; partial ||w||^2   (vprev may be null).  fp64 vectors in fp64;
+// fp32 vectors in double-float (a and b split into two fp32 words each, exact products),
+// rounded once, with the norm's per-thread sum in double-float as well: the fp64 pipe of
+// this GPU is too slow for a pass over the whole vector.
 template <typename V>
 __global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, double b,
                                  int64_t n, double *partial) {
   using A = typename Vt<V>::A;
+  constexpr bool kF = sizeof(A) == 4;
   double acc = 0;
+  float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f, nh = 0.f, nl = 0.f;
+  if constexpr (kF) {
+    df_split(a, ah, al);
+    df_split(b, bh, bl);
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if constexpr (Vt<V>::cplx) {
+    if constexpr (Vt<V>::cplx && kF) {
       // a and b are real (Hermitian tridiagonal)
+      const V w0 = w[i], v0 = v[i];
+      float rh = w0.x, rl = 0.f, ih = w0.y, il = 0.f;
+      df_sub_scaled(rh, rl, ah, al, v0.x);
+      df_sub_scaled(ih, il, ah, al, v0.y);
+      if (vprev) {
+        const V p0 = vprev[i];
+        df_sub_scaled(rh, rl, bh, bl, p0.x);
+        df_sub_scaled(ih, il, bh, bl, p0.y);
+      }
+      V o; o.x = df_round(rh, rl); o.y = df_round(ih, il);
+      w[i] = o;
+      df_add_prod(nh, nl, o.x, o.x);
+      df_add_prod(nh, nl, o.y, o.y);
+    } else if constexpr (kF) {
+      float hi = w[i], lo = 0.f;
+      df_sub_scaled(hi, lo, ah, al, v[i]);
+      if (vprev) df_sub_scaled(hi, lo, bh, bl, vprev[i]);
+      const float o = df_round(hi, lo);
+      w[i] = o;
+      df_add_prod(nh, nl, o, o);
+    } else if constexpr (Vt<V>::cplx) {
       double wr = (double)w[i].x - a * (double)v[i].x;
       double wi = (double)w[i].y - a * (double)v[i].y;
       if (vprev) { wr -= b * (double)vprev[i].x; wi -= b * (double)vprev[i].y; }
@@ -287,6 +318,7 @@ __global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, dou
       acc += (double)o * (double)o;
     }
   }
+  if constexpr (kF) acc = df_value(nh, nl);
   block_reduce_store<double>(acc, partial, blockIdx.x);
 }
 

@@ -22,6 +22,7 @@
 // (two-float) accumulator, fp64 in fp64.  Each y_i written once; no atomics.
 #include "sced_internal.cuh"
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 namespace {
@@ -59,6 +60,14 @@ struct TwoParams {
   uint32_t n_e1, n_e2, n_rid, n_dest, n_bond, n_top, n_sq, n_cs;
   uint32_t off_bblk, off_e2, off_e1, off_rid, off_dest, off_src, off_phase, off_bond, off_top, off_sq, off_cs,
       smem_bytes;
+  // term-parallel kernel: fp32 norm / character tables and the per-warp row states and
+  // term lists (0 when the layout has no tile region)
+  uint32_t off_sqf, off_csf, off_tile, tile_warps;
+  const uint32_t *nib;           // antiparallel masks by nibbles, [word][n_nib][16]
+  uint32_t n_nib, off_nib;
+  const uint4 *rlim;             // ranked Limits records (null: search the buckets)
+  int rq_bits, rpost_bits;
+  uint32_t rqmask, rpmask;
 };
 
 struct Sm2 {
@@ -69,6 +78,10 @@ struct Sm2 {
   const uint8_t *rid, *dest, *src, *bond;
   const int32_t *phase;
 };
+
+// per-warp shared memory of the term-parallel kernel: 32 row states, 32 row accumulators
+// (real and imaginary parts), then a list of at most 32 x 16 terms of 16 bits
+constexpr uint32_t kTileWarpBytes = 32 * 8 + 32 * 8 + 32 * 16 * 2;
 
 struct Rep2 {
   uint32_t minrep;   // top block of the representative
@@ -275,6 +288,25 @@ __device__ __forceinline__ int64_t lookup_two(const Sm2 &S, const TwoParams &P, 
   return -1;
 }
 
+// Index of the representative through the ranked Limits: one 16-byte record per key
+// {first index of the bucket, 0, bitmap of the postfixes present}; the state is present
+// when its postfix bit is set, and its index is the first index plus the number of
+// present postfixes below it.  One dependent global load instead of a binary search.
+__device__ __forceinline__ int64_t lookup_ranked(const Sm2 &S, const TwoParams &P,
+                                                 uint32_t minrep, uint32_t low) {
+  const uint64_t r = ((uint64_t)minrep << P.L) | low;
+  const uint32_t rk = S.top[(uint32_t)(r >> (P.N - P.r_bits))];
+  if (rk == 0xFFFFu) return -1;
+  const uint32_t key = (rk << P.rq_bits) | ((uint32_t)(r >> P.rpost_bits) & P.rqmask);
+  uint4 rec;
+  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(rec.x), "=r"(rec.y), "=r"(rec.z), "=r"(rec.w) : "l"(P.rlim + key));
+  const uint32_t pf = (uint32_t)r & P.rpmask;
+  const uint64_t bits = ((uint64_t)rec.w << 32) | rec.z;
+  if (!((bits >> pf) & 1ULL)) return -1;
+  return (int64_t)rec.x + __popcll(bits & ((1ULL << pf) - 1ULL));
+}
+
 // Kernel without level-2 tables in shared memory: two 768-thread blocks per SM, i.e. 48
 // warps at 40 registers.  48 warps hide more of the dependent table loads than 32 at 64
 // registers; and two blocks stage the shared tables twice where three 512-thread blocks
@@ -418,6 +450,334 @@ __global__ void __launch_bounds__(kE2 ? 1024 : kThreads, kE2 ? 1 : kMinBlocks) a
   }
 }
 
+constexpr int kTileChunk = 16;
+constexpr int kTileThreads = 768;      // level-2 tables in global memory: 2 blocks per SM
+constexpr int kTileMinBlocks = 2;
+constexpr int kTileThreadsE2 = 1024;   // level-2 tables staged: 1 block per SM
+
+// The common cases of the two-level search, without loops: one minimal block at level 1
+// and one or two candidates at level 2 (a Sym^R list of one or two elements; two equal
+// images are a stabiliser of order 2, whose characters must agree).  Returns false,
+// leaving R unset, when the term needs the general search (several minimal blocks,
+// several level-2 minimal blocks, or a longer Sym^R list).
+template <int NSUB, bool kE2>
+__device__ __forceinline__ bool find_rep_simple(const Sm2 &S, const TwoParams &P,
+                                                const uint32_t (&sub)[NSUB], Rep2 &R) {
+  const int n = P.n;
+  // level 1: only the entry of the minimal block is kept (one minimal block is the case
+  // handled here)
+  uint32_t minrep = 0xFFFFFFFFu, ymask = 0, eY = 0;
+#pragma unroll
+  for (int X = 0; X < NSUB; X++) {
+    const uint32_t ex = S.e1[(X << n) | sub[X]];
+    const uint32_t r = ex & 0xFFFu;
+    if (r < minrep) { minrep = r; ymask = 1u << X; eY = ex; }
+    else if (r == minrep) ymask |= 1u << X;
+  }
+  if (ymask & (ymask - 1)) return false;
+  const int h = (eY >> 12) & 0xFFF;
+  uint32_t tau[NSUB];
+  tau[0] = minrep;
+#pragma unroll
+  for (int d = 1; d < NSUB; d++) {
+    const int X = S.src[h * NSUB + d];
+    tau[d] = act(P, X, pick<NSUB>(sub, X), h);
+  }
+  const int phh = S.phase[h];
+  R.minrep = minrep;
+  R.t = 1;
+  R.mixed = 0;
+  const int rid = S.rid[minrep];
+  if (rid == 0xFF) {   // K_R = {e}: h is the only candidate
+    uint32_t low = 0;
+#pragma unroll
+    for (int d = 1; d < NSUB; d++) low |= tau[d] << ((NSUB - 1 - d) * n);
+    R.low = low;
+    R.ph = phh;
+    return true;
+  }
+  // level 2: again only the entry of the minimal block is kept
+  const uint32_t rbase = (uint32_t)rid * (NSUB - 1);
+  uint32_t m2 = 0xFFFFFFFFu, dmask = 0, fd = 0;
+  int d2 = 1;
+#pragma unroll
+  for (int d = 1; d < NSUB; d++) {
+    const uint32_t ei = ((rbase + d - 1) << n) | tau[d];
+    const uint32_t fv = kE2 ? S.e2[ei] : __ldg(P.e2 + ei);
+    const uint32_t r2 = fv & 0xFFFu;
+    if (r2 < m2) { m2 = r2; dmask = 1u << d; fd = fv; d2 = d; }
+    else if (r2 == m2) dmask |= 1u << d;
+  }
+  const uint32_t cnt = fd >> 24;
+  if ((dmask & (dmask - 1)) || cnt > 2) return false;
+  const int k = (int)((fd >> 12) & 0xFFF);
+  uint32_t low = m2 << ((NSUB - 2) * n);
+  const uint32_t low2 = low;
+#pragma unroll
+  for (int d = 1; d < NSUB; d++) {
+    if (d == d2) continue;
+    const int dd = S.dest[k * NSUB + d];
+    low |= act(P, d, tau[d], k) << ((NSUB - 1 - dd) * n);
+  }
+  int ph = phh + S.phase[k];
+  if (ph >= P.denom) ph -= P.denom;
+  R.low = low;
+  R.ph = ph;
+  if (cnt == 2) {   // Sym^R holds a second element: compare its image, count a tie
+    const uint32_t base = __ldg(P.off2 + (((rbase + d2 - 1) << n) | pick<NSUB>(tau, d2)));
+    const int k2 = (int)__ldg(P.list2 + base + 1);
+    uint32_t lowb = low2;
+#pragma unroll
+    for (int d = 1; d < NSUB; d++) {
+      if (d == d2) continue;
+      const int dd = S.dest[k2 * NSUB + d];
+      lowb |= act(P, d, tau[d], k2) << ((NSUB - 1 - dd) * n);
+    }
+    int phb = phh + S.phase[k2];
+    if (phb >= P.denom) phb -= P.denom;
+    if (lowb < low) {
+      R.low = lowb;
+      R.ph = phb;
+    } else if (lowb == low) {
+      R.t = 2;
+      R.mixed = phb != ph;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Term-parallel product (fp32 and complex fp32 vectors).
+//
+// A warp owns a tile of 32 consecutive rows (lane l owns row l of the tile).  The bonds
+// are taken in chunks of 16 (half a padded word, one coupling class); for each chunk
+// every lane appends its row's antiparallel bonds to a warp-private list in shared
+// memory, in row order, and the warp then works through the list 32 terms at a time:
+// lane l takes term base + l whatever row it belongs to.  Rows of unequal length no
+// longer leave lanes idle (a row-per-lane loop runs as long as the longest row of the
+// warp).
+//
+// A term whose search needs more than the common case (several minimal blocks or
+// several level-2 candidates, see find_rep_simple) is not resolved in its round: it is
+// appended to a second list (written over the part of the chunk list already consumed)
+// and the deferred terms are resolved together, 32 at a time, by the general search.
+// The rare long searches then run with every lane busy instead of stalling 31 lanes of
+// each round.  Both lists stay in row order.
+//
+// A term's value goes back to its row by a segmented inclusive scan over the 32 lanes
+// (rows are non-decreasing along a list, so equal neighbouring rows form one segment);
+// the lane holding a segment's last term adds the sum to the row's shared accumulator.
+// Every step has a fixed order, so the product is deterministic; no atomics.
+// ---------------------------------------------------------------------------------------
+template <typename V, int NSUB, bool kE2, bool kGeneral>
+__device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, const V *x,
+                                           const float *sqf, const float *csf,
+                                           const uint64_t *rowst, uint16_t *list, int base,
+                                           int T, int bbase, float jhc, float *racc, int *n_def) {
+  constexpr bool kC = Vf<V>::cplx;
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  const int N = P.N, n = P.n;
+  const uint32_t bmask = (1u << n) - 1u;
+  const int t = base + lane;
+  int r = 32;
+  uint32_t e = 0;
+  bool defer = false;
+  float v_re = 0.f, v_im = 0.f;
+  if (t < T) {
+    e = list[t];
+    r = (int)(e >> 5);
+    const uint64_t sr = rowst[r];
+    // the exchanged configuration, block by block: one bit flips in the block of each
+    // end of the bond
+    const uint32_t bi = S.bblk[bbase + (e & 31)];
+    const int xa = bi & 15, xb = (bi >> 4) & 15;
+    const uint32_t fa = 1u << ((bi >> 8) & 255), fb = 1u << (bi >> 16);
+    uint32_t s2[NSUB];
+#pragma unroll
+    for (int X = 0; X < NSUB; X++)
+      s2[X] = ((uint32_t)(sr >> (N - (X + 1) * n)) & bmask) ^ (X == xa ? fa : 0u) ^
+              (X == xb ? fb : 0u);
+    Rep2 R;
+    if constexpr (kGeneral) {
+      R = find_rep_blocks<NSUB, kE2>(S, P, s2);
+    } else {
+      defer = !find_rep_simple<NSUB, kE2>(S, P, s2, R);
+    }
+    if (!defer && !R.mixed) {
+      const int64_t j = P.rlim ? lookup_ranked(S, P, R.minrep, R.low) : lookup_two(S, P, R.minrep, R.low);
+      if (j >= 0) {
+        const V xj = gather_x(x, j);
+        const float wgt = R.t == 1 ? jhc : jhc * sqf[R.t];   // J_c / 2 sqrt(|Stab_j|)
+        if constexpr (!kC) {
+          const float pv = wgt * xj;
+          v_re = R.ph == 0 ? pv : -pv;
+        } else {
+          const float cr = csf[2 * R.ph] * wgt, ci = csf[2 * R.ph + 1] * wgt;
+          v_re = cr * xj.x - ci * xj.y;
+          v_im = cr * xj.y + ci * xj.x;
+        }
+      }
+    }
+  }
+  if constexpr (!kGeneral) {
+    // deferred terms go, in lane (= list) order, to the front of the list, over entries
+    // every lane has read already (one deferred entry per consumed entry at most)
+    const unsigned dm = __ballot_sync(FULL, defer);
+    if (defer) list[*n_def + __popc(dm & ((1u << lane) - 1u))] = (uint16_t)e;
+    *n_def += __popc(dm);
+  }
+  // segmented inclusive scan: lanes with the same row form one segment
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int ru = __shfl_up_sync(FULL, r, d);
+    const float a = __shfl_up_sync(FULL, v_re, d);
+    float b = 0.f;
+    if constexpr (kC) b = __shfl_up_sync(FULL, v_im, d);
+    if (lane >= d && ru == r) {
+      v_re += a;
+      if constexpr (kC) v_im += b;
+    }
+  }
+  const int rn = __shfl_down_sync(FULL, r, 1);
+  __syncwarp();   // the previous round's accumulator updates are visible
+  if (r < 32 && (lane == 31 || rn != r)) {   // last lane of its segment
+    racc[r] += v_re;
+    if constexpr (kC) racc[32 + r] += v_im;
+  }
+}
+
+template <typename V, int NSUB, bool kE2>
+__global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 : kTileMinBlocks)
+    apply_tile_kernel(const __grid_constant__ TwoParams P) {
+  constexpr bool kC = Vf<V>::cplx;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const Sm2 S = stage_two(P, sm, kC, kE2);
+  {
+    const double *sqd = reinterpret_cast<const double *>(sm + P.off_sq);
+    const double *csd = reinterpret_cast<const double *>(sm + P.off_cs);
+    float *sqf = reinterpret_cast<float *>(sm + P.off_sqf);
+    float *csf = reinterpret_cast<float *>(sm + P.off_csf);
+    for (uint32_t k = threadIdx.x; k < P.n_sq; k += blockDim.x) sqf[k] = (float)sqd[k];
+    if (kC) for (uint32_t k = threadIdx.x; k < P.n_cs; k += blockDim.x) csf[k] = (float)csd[k];
+    uint32_t *nb = reinterpret_cast<uint32_t *>(sm + P.off_nib);
+    const uint32_t n_nibtab = (uint32_t)P.cls_word[P.n_classes] * P.n_nib * 16;
+    for (uint32_t k = threadIdx.x; k < n_nibtab; k += blockDim.x) nb[k] = P.nib[k];
+    __syncthreads();
+  }
+  const uint32_t *nibs = reinterpret_cast<const uint32_t *>(sm + P.off_nib);
+  const float *sqf = reinterpret_cast<const float *>(sm + P.off_sqf);
+  const float *csf = reinterpret_cast<const float *>(sm + P.off_csf);
+  const double *rsd = reinterpret_cast<const double *>(sm + P.off_sq) + P.n_sq;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char *tw = sm + P.off_tile + (size_t)wid * kTileWarpBytes;
+  uint64_t *rowst = reinterpret_cast<uint64_t *>(tw);
+  float *racc = reinterpret_cast<float *>(tw + 32 * 8);            // [2][32] re, im
+  uint16_t *list = reinterpret_cast<uint16_t *>(tw + 32 * 8 + 32 * 8);
+  const V *x = reinterpret_cast<const V *>(P.x);
+  V *y = reinterpret_cast<V *>(P.y);
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int64_t n_tiles = (P.r1 - P.r0 + 31) >> 5;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  double dot_re = 0.0, dot_im = 0.0;
+  for (int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; tile < n_tiles; tile += wstride) {
+    {
+      const int64_t i = P.r0 + (tile << 5) + lane;
+      rowst[lane] = i < P.r1 ? __ldcs(reinterpret_cast<const unsigned long long *>(P.basis) + i) : 0ULL;
+      racc[lane] = 0.f;
+      if (kC) racc[32 + lane] = 0.f;
+    }
+    const bool valid = P.r0 + (tile << 5) + lane < P.r1;
+    double diag = 0.0;
+    for (int c = 0; c < P.n_classes; c++) {
+      const float jhc = (float)P.jh[c];
+      int nanti = 0;
+      for (int wd = P.cls_word[c]; wd < P.cls_word[c + 1]; wd++) {
+        uint32_t m = 0;
+        {   // antiparallel bonds of the word: XOR of the state's nibbles' contributions
+          const uint64_t s = rowst[lane];
+          const uint32_t *nw = nibs + (uint32_t)wd * P.n_nib * 16;
+          for (uint32_t q = 0; q < P.n_nib; q++) m ^= nw[q * 16 + (uint32_t)((s >> (4 * q)) & 15u)];
+        }
+        if (!valid) m = 0;
+        nanti += __popc(m);
+#pragma unroll 1
+        for (int h = 0; h < 32 / kTileChunk; h++) {
+          const uint32_t cm = (m >> (kTileChunk * h)) & ((1u << kTileChunk) - 1u);
+          const int cnt = __popc(cm);
+          int incl = cnt;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += u;
+          }
+          const int T = __shfl_sync(FULL, incl, 31);
+          if (T == 0) continue;
+          {   // this lane's terms, in bond order, at its place in the row-major list
+            uint32_t mm = cm;
+            int pos = incl - cnt;
+            while (mm) {
+              const int k = __ffs(mm) - 1;
+              mm &= mm - 1;
+              list[pos++] = (uint16_t)((lane << 5) | k);
+            }
+          }
+          __syncwarp();
+          const int bbase = wd * 32 + kTileChunk * h;
+          int n_def = 0;
+          for (int base = 0; base < T; base += 32)
+            tile_round<V, NSUB, kE2, false>(S, P, x, sqf, csf, rowst, list, base, T, bbase, jhc, racc, &n_def);
+          __syncwarp();
+          for (int base = 0; base < n_def; base += 32)
+            tile_round<V, NSUB, kE2, true>(S, P, x, sqf, csf, rowst, list, base, n_def, bbase, jhc, racc, &n_def);
+          __syncwarp();   // the list is rewritten by the next chunk
+        }
+      }
+      diag += P.jzq[c] * (double)(P.nb_cls[c] - 2 * nanti);
+    }
+    __syncwarp();
+    if (valid) {
+      const int64_t i = P.r0 + (tile << 5) + lane;
+      const double rs = rsd[__ldcs(P.stab + i)];
+      const double row_re = (double)racc[lane];
+      if constexpr (!kC) {
+        const double xi = (double)x[i];
+        const float yi = (float)(diag * xi + row_re * rs);
+        __stcs(y + (i - P.r0), yi);
+        if (P.partial) dot_re += xi * (double)yi;
+      } else {
+        const double row_im = (double)racc[32 + lane];
+        const V xv = x[i];
+        V yv;
+        yv.x = (float)(diag * (double)xv.x + row_re * rs);
+        yv.y = (float)(diag * (double)xv.y + row_im * rs);
+        y[i - P.r0] = yv;
+        if (P.partial) {
+          dot_re += (double)xv.x * yv.x + (double)xv.y * yv.y;
+          dot_im += (double)xv.x * yv.y - (double)xv.y * yv.x;
+        }
+      }
+    }
+    __syncwarp();   // rowst and racc are rewritten by the next tile
+  }
+  if (P.partial) {
+    __shared__ double red[32];
+    const int nparts = kC ? 2 : 1;
+    for (int part = 0; part < nparts; part++) {
+      double d = part ? dot_im : dot_re;
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(FULL, d, o);
+      __syncthreads();
+      if (lane == 0) red[wid] = d;
+      __syncthreads();
+      if (wid == 0) {
+        d = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(FULL, d, o);
+        if (lane == 0) P.partial[part * gridDim.x + blockIdx.x] = d;
+      }
+    }
+  }
+}
+
 // test hook: the two-level search alone
 template <int NSUB, bool kE2>
 __global__ void find_rep_two_kernel(const TwoParams P, const DevIndex I, const uint64_t *states,
@@ -443,7 +803,8 @@ __global__ void find_rep_two_kernel(const TwoParams P, const DevIndex I, const u
 size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Parameters and shared-memory layout; e2 = stage the level-2 tables in shared memory.
-int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, TwoParams &P) {
+int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, TwoParams &P,
+                int tile_warps = 0) {
   if (!B->two_level || B->nsub < 2 || B->nsub > 4 || B->I.r_bits > 12 || B->D == 0 ||
       (B->nsub - 1) * B->n > 32 || B->N - B->I.r_bits > 32)
     return ED_ERR_UNSUPPORTED;
@@ -491,8 +852,22 @@ int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, T
   put(P.off_dest, P.n_dest);
   put(P.off_src, P.n_dest);
   put(P.off_bond, P.n_bond);
+  P.tile_warps = (uint32_t)tile_warps;
+  P.rlim = reinterpret_cast<const uint4 *>(B->d_rlim);
+  P.rq_bits = B->rq_bits;
+  P.rpost_bits = B->rpost_bits;
+  P.rqmask = B->rq_bits >= 32 ? 0xFFFFFFFFu : ((1u << B->rq_bits) - 1u);
+  P.rpmask = (1u << B->rpost_bits) - 1u;
+  P.nib = B->d_nib;
+  P.n_nib = (uint32_t)B->n_nib;
+  if (tile_warps) {
+    put(P.off_sqf, 4 * (size_t)P.n_sq);
+    put(P.off_csf, 4 * (size_t)P.n_cs);
+    put(P.off_nib, 4 * B->nib.size());
+    put(P.off_tile, (size_t)tile_warps * kTileWarpBytes);
+  }
   P.smem_bytes = (uint32_t)off;
-  if (off > (e2 ? 180 : 100) * 1024) return ED_ERR_UNSUPPORTED;
+  if (off > (e2 ? (tile_warps ? 220 : 180) : 100) * 1024) return ED_ERR_UNSUPPORTED;
   return ED_OK;
 }
 
@@ -531,6 +906,34 @@ int launch_v(const TwoParams &P, bool e2, int nsub, int grid, cudaStream_t st) {
 
 }  // namespace
 
+template <typename V, int NSUB>
+int launch_tile_t(const TwoParams &P, bool e2, int grid, cudaStream_t st) {
+  if (e2) {
+    auto k = apply_tile_kernel<V, NSUB, true>;
+    ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
+    k<<<grid, kTileThreadsE2, P.smem_bytes, st>>>(P);
+  } else {
+    auto k = apply_tile_kernel<V, NSUB, false>;
+    ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem_bytes));
+    const int need = kTileMinBlocks * ((int)P.smem_bytes + 1536);
+    const int pct = std::min(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
+    ED_CK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    k<<<grid, kTileThreads, P.smem_bytes, st>>>(P);
+  }
+  ED_CK(cudaGetLastError());
+  return ED_OK;
+}
+
+template <typename V>
+int launch_tile_v(const TwoParams &P, bool e2, int nsub, int grid, cudaStream_t st) {
+  switch (nsub) {
+    case 2: return launch_tile_t<V, 2>(P, e2, grid, st);
+    case 3: return launch_tile_t<V, 3>(P, e2, grid, st);
+    case 4: return launch_tile_t<V, 4>(P, e2, grid, st);
+  }
+  return ED_ERR_UNSUPPORTED;
+}
+
 // The two-level path applies when its tables exist (2..4 sublattices of <= 11 sites,
 // |G| <= 4096); returns ED_ERR_UNSUPPORTED otherwise (the caller uses the generic kernel).
 int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
@@ -541,6 +944,29 @@ int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, c
   int rc = make_params(B, J, Jz, e2, P);
   if (rc == ED_ERR_UNSUPPORTED) { e2 = false; rc = make_params(B, J, Jz, false, P); }
   if (rc) return rc;
+  // fp32 vectors: the term-parallel kernel (level-2 tables staged when they fit with the
+  // per-warp term lists, else read from global memory)
+  if (mode == 0 && (dtype == ED_F32 || dtype == ED_C64) && !getenv("SCED_ROW_KERNEL")) {
+    TwoParams Q;
+    bool qe2 = e2;
+    int qrc = make_params(B, J, Jz, qe2, Q, (qe2 ? kTileThreadsE2 : kTileThreads) / 32);
+    if (qrc == ED_ERR_UNSUPPORTED && qe2) {
+      qe2 = false;
+      qrc = make_params(B, J, Jz, false, Q, kTileThreads / 32);
+    }
+    if (qrc == ED_OK) {
+      Q.x = x; Q.y = y; Q.r0 = r0; Q.r1 = r1; Q.partial = partial;
+      const int bs = qe2 ? kTileThreadsE2 : kTileThreads;
+      int grid = B->sm_count * (qe2 ? 1 : kTileMinBlocks);
+      const int64_t need = (r1 - r0 + bs - 1) / bs;
+      if (need < grid) grid = (int)need;
+      if (grid < 1) grid = 1;
+      if (partial && grid > B->n_partial / 2) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
+      B->last_apply_grid = grid;
+      return dtype == ED_F32 ? launch_tile_v<float>(Q, qe2, B->nsub, grid, st)
+                             : launch_tile_v<float2>(Q, qe2, B->nsub, grid, st);
+    }
+  }
   P.x = x; P.y = y; P.r0 = r0; P.r1 = r1; P.partial = partial;
   const int bs = e2 ? 1024 : kThreads;
   int grid = B->sm_count * (e2 ? 1 : kMinBlocks);

@@ -248,6 +248,41 @@ __global__ void make_limits(const uint64_t *basis, int64_t D, const uint32_t *ra
   }
 }
 
+// Ranked Limits (Sec. IV's Limits with the in-bucket search replaced by a rank): with at
+// most 6 postfix bits a bucket is a subset of 64 values, kept as a 64-bit occupancy
+// bitmap next to the bucket's first index; the index of a state is then
+// start + popcount(bitmap below its postfix).  One 16-byte record per key:
+// {start, 0, bitmap low word, bitmap high word}.
+__global__ void ranked_starts(const uint64_t *basis, int64_t D, const uint32_t *rank_top,
+                              int r_shift, int q_bits, int post_bits, uint64_t n_keys,
+                              uint4 *rec) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_keys;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t rk = k >> q_bits;
+    const uint64_t mid = k & ((1ULL << q_bits) - 1ULL);
+    const uint64_t thr = ((uint64_t)rank_top[rk] << r_shift) | (mid << post_bits);
+    int64_t lo = 0, hi = D;
+    while (lo < hi) {
+      const int64_t m = (lo + hi) >> 1;
+      if (basis[m] < thr) lo = m + 1; else hi = m;
+    }
+    rec[k] = make_uint4((uint32_t)lo, 0u, 0u, 0u);
+  }
+}
+
+__global__ void ranked_bits(const uint64_t *basis, int64_t D, const uint32_t *top_rank,
+                            int r_shift, int q_bits, int post_bits, uint4 *rec) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = basis[i];
+    const uint64_t rk = top_rank[s >> r_shift];
+    const uint64_t k = (rk << q_bits) | ((s >> post_bits) & ((1ULL << q_bits) - 1ULL));
+    const uint32_t pf = (uint32_t)(s & ((1ULL << post_bits) - 1ULL));
+    unsigned int *w = reinterpret_cast<unsigned int *>(rec + k) + (pf < 32 ? 2 : 3);
+    atomicOr(w, 1u << (pf & 31));
+  }
+}
+
 __global__ void max_bucket_kernel(const uint32_t *limits, uint64_t n_keys,
                                   unsigned long long *out) {
   unsigned long long m = 0;
@@ -472,6 +507,29 @@ int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target) {
       make_postfix<uint32_t><<<g1, 256, 0, st>>>(B->d_basis, B->D, pmask, (uint32_t *)B->d_postfix);
     ED_CK(cudaGetLastError());
   }
+  // ranked Limits: 6 postfix bits (fewer when N - r_bits < 6), if the records fit (one
+  // record per key; at most 2^32 keys and 16 bytes per key, no more than 4x the basis)
+  {
+    const int rq = std::max(0, N - r_bits - 6);
+    const int rpost = N - r_bits - rq;
+    const uint64_t rkeys = R << rq;
+    if (rkeys < (1ULL << 32) && rkeys * 16 <= std::max<uint64_t>(4 * (uint64_t)D * 8, 1ULL << 26)) {
+      if (cudaMalloc(&B->d_rlim, rkeys * 16) == cudaSuccess) {
+        ranked_starts<<<g1, 256, 0, st>>>(B->d_basis, B->D, d_rank_top, N - r_bits, rq, rpost, rkeys,
+                                          reinterpret_cast<uint4 *>(B->d_rlim));
+        ED_CK(cudaGetLastError());
+        ranked_bits<<<g1, 256, 0, st>>>(B->d_basis, B->D, B->d_top_rank, N - r_bits, rq, rpost,
+                                        reinterpret_cast<uint4 *>(B->d_rlim));
+        ED_CK(cudaGetLastError());
+        B->rq_bits = rq;
+        B->rpost_bits = rpost;
+        B->n_rkeys = (int64_t)rkeys;
+      } else {
+        cudaGetLastError();   // no ranked index: the kernels search the buckets instead
+        B->d_rlim = nullptr;
+      }
+    }
+  }
   ED_CK(cudaFreeAsync(d_flags, st));
   ED_CK(cudaFreeAsync(d_scan, st));
   ED_CK(cudaFreeAsync(d_rank_top, st));
@@ -479,7 +537,8 @@ int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target) {
   ED_CK(cudaStreamSynchronize(st));
   B->n_keys = (int64_t)n_keys;
   B->max_bucket = (int64_t)mb;
-  B->index_bytes = ntop * 4 + (n_keys + 1) * 4 + (post_bytes == 8 ? 0 : (size_t)D * post_bytes);
+  B->index_bytes = ntop * 4 + (n_keys + 1) * 4 + (post_bytes == 8 ? 0 : (size_t)D * post_bytes) +
+                   (size_t)B->n_rkeys * 16;
   DevIndex &I = B->I;
   I.N = N;
   I.r_bits = r_bits;

@@ -184,6 +184,21 @@ int validate(ed_basis *B, const ed_lattice *L, const ed_group *G, const ed_irrep
     B->bond_blk[b] = (uint32_t)(la / n) | ((uint32_t)(lb / n) << 4) |
                      ((uint32_t)(n - 1 - la % n) << 8) | ((uint32_t)(n - 1 - lb % n) << 16);
   }
+  // Antiparallel masks by nibbles: bit k of word w is s_a XOR s_b for bond k = (a, b), a
+  // linear map of the state's bits over GF(2), so the mask is the XOR over the state's
+  // 4-bit nibbles q of nib[(w * n_nib + q) * 16 + nibble_q(s)], where each entry XORs in
+  // bit k for every endpoint of bond k that lies in nibble q and is up.
+  const int n_words = B->cls_word[B->n_classes];
+  B->n_nib = (N + 3) / 4;
+  B->nib.assign((size_t)n_words * B->n_nib * 16, 0u);
+  for (int w = 0; w < n_words; w++)
+    for (int k = 0; k < 32; k++) {
+      const int pa = B->bond_pad[2 * (w * 32 + k)], pb = B->bond_pad[2 * (w * 32 + k) + 1];
+      if (pa == pb) continue;   // inert padding
+      for (int p : {pa, pb})
+        for (int v = 0; v < 16; v++)
+          if ((v >> (p % 4)) & 1) B->nib[((size_t)w * B->n_nib + p / 4) * 16 + v] ^= 1u << k;
+    }
   return ED_OK;
 }
 
@@ -211,6 +226,7 @@ int build_norm_tables(ed_basis *B, cudaStream_t st) {
   if ((rc = up((void **)&B->d_bond_pos, B->bond_pos.data(), B->bond_pos.size()))) return rc;
   if ((rc = up((void **)&B->d_bond_pad, B->bond_pad.data(), B->bond_pad.size()))) return rc;
   if ((rc = up((void **)&B->d_bond_blk, B->bond_blk.data(), B->bond_blk.size() * 4))) return rc;
+  if ((rc = up((void **)&B->d_nib, B->nib.data(), B->nib.size() * 4))) return rc;
   ED_CK(cudaStreamSynchronize(st));
   return ED_OK;
 }
@@ -396,8 +412,8 @@ int build_tables(ed_basis *B, cudaStream_t st, const ed_basis *share) {
 void free_all(ed_basis *B) {
   void *ptrs[] = {B->d_rep, B->d_sym_off, B->d_sym_list, B->d_action, B->d_dest, B->d_phase,
                   B->d_src, B->d_e1, B->d_rid, B->d_e2, B->d_off2, B->d_list2, B->d_bond_pad,
-                  B->d_bond_blk, B->d_pbit, B->d_flip,
-                  B->d_basis, B->d_stab, B->d_top_rank, B->d_limits,
+                  B->d_bond_blk, B->d_nib, B->d_pbit, B->d_flip,
+                  B->d_basis, B->d_stab, B->d_top_rank, B->d_limits, B->d_rlim,
                   B->d_postfix == B->d_basis ? nullptr : B->d_postfix,
                   B->d_sqrt, B->d_rsqrt, B->d_cs, B->d_bond_pos, B->d_partial,
                   B->d_stage_x, B->d_stage_y};

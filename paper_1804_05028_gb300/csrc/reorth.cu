@@ -4,18 +4,24 @@
 //
 // After the three-term update w = H v_j - alpha_j v_j - beta_{j-1} v_{j-1}, a
 // Gram-Schmidt sweep against m vectors u_0 .. u_{m-1} computes c_k = <u_k, w> and then
-// w <- w - sum_k c_k u_k with ||w||^2.  Vectors may be fp32 or fp64 (real or complex);
-// every dot, every coefficient and the update are accumulated in fp64 and w is rounded
-// once.  Reductions run in a fixed order (per warp, then per block, then over blocks),
-// so a sweep is bit-for-bit reproducible -- the second Lanczos pass that rebuilds the
-// ground state relies on that.
+// w <- w - sum_k c_k u_k with ||w||^2.  Vectors may be fp32 or fp64 (real or complex).
+// With fp64 vectors every operation is fp64.  With fp32 vectors the per-thread sums run
+// in double-float (dfloat.cuh: exact fp32 products, about 48 significant bits; this
+// GPU's fp64 pipe is far too slow for a sweep over 10^9 products), the coefficients are
+// fp64 and split into two fp32 words for the update, and all cross-thread reductions are
+// fp64; w is rounded once.  Reductions run in a fixed order (per warp, then per block,
+// then over blocks), so a sweep is bit-for-bit reproducible -- the second Lanczos pass
+// that rebuilds the ground state relies on that.
 //
 // Kernels (all HBM streams, no tensor cores: m dot products and one m-term axpy):
-//   multidot_kernel   partial[k][blk] = sum over the block's rows of conj(u_k) w
+//   multidot_kernel   partial[k][blk] = sum over the block's rows of conj(u_k) w, for
+//                     groups of 8 vectors (one group per blockIdx.y)
 //   coef_kernel       c[k] = sum over blocks of partial[k][.], one block per k
 //   update_kernel     w -= sum_k c_k u_k, partial ||w||^2 per block
 //   combine_kernel    psi = sum_k s_k u_k (the Ritz vector from a stored Krylov basis)
 #include "sced_internal.cuh"
+#include "dfloat.cuh"
+#include <type_traits>
 
 namespace {
 
@@ -27,7 +33,7 @@ template <> struct Rv<float2> { using A = float; static constexpr bool cplx = tr
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kRows = 8;      // rows per lane in one pass of a warp over its chunk
+constexpr int kGroup = 8;     // vectors per block of the multi-dot (blockIdx.y)
 
 // the m vectors: base + k * stride (a Krylov store), or the two explicit pointers p0, p1
 struct VecSet {
@@ -48,60 +54,67 @@ __device__ __forceinline__ double warp_sum(double d) {
   return d;
 }
 
-// Each warp walks chunks of 32 * kRows rows (grid-stride over chunks), holding w in
-// registers; for every k it reduces conj(u_k) w over the chunk and lane 0 adds the sum to
-// its own shared slot acc[k][warp].  At the end the block sums its warps' slots in warp
-// order into partial[(k * P + part) * nblk + blk], P = 2 for complex (re, im) else 1.
+// Every thread keeps accumulators for a group of kGroup vectors (blockIdx.y selects the
+// group) over its grid-stride rows: w[i] is read once per group and the kGroup loads of
+// u_k[i] are independent.  fp32 vectors accumulate exact products in double-float, fp64
+// vectors in fp64.  At the end the block reduces each accumulator in fp64 (warps, then the
+// block's warps in order) into partial[(k * P + part) * nblk + blk], P = 2 for complex
+// (re, im) else 1.
 template <typename V>
 __global__ void __launch_bounds__(kThreads) multidot_kernel(VecSet S, const V *w, int64_t n,
                                                             double *partial) {
+  using A = typename Rv<V>::A;
   constexpr bool kC = Rv<V>::cplx;
+  constexpr bool kF = std::is_same<A, float>::value;
   constexpr int P = kC ? 2 : 1;
-  extern __shared__ double acc[];   // [m][P][kWarps]
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int t = threadIdx.x; t < S.m * P * kWarps; t += kThreads) acc[t] = 0.0;
-  __syncthreads();
-  const int64_t chunk = 32 * kRows;
-  const int64_t n_chunks = (n + chunk - 1) / chunk;
-  for (int64_t c = (int64_t)blockIdx.x * kWarps + wid; c < n_chunks;
-       c += (int64_t)gridDim.x * kWarps) {
-    const int64_t r0 = c * chunk + lane;
-    V wv[kRows];
+  __shared__ double red[kGroup * P][kWarps];
+  const int k0 = blockIdx.y * kGroup;
+  const int kn = min(kGroup, S.m - k0);
+  double re[kGroup], im[kGroup];        // fp64 vectors
+  float rh[kGroup], rl[kGroup], ih[kGroup], il[kGroup];   // fp32 vectors: double-float
 #pragma unroll
-    for (int r = 0; r < kRows; r++) {
-      const int64_t i = r0 + 32 * r;
-      if (i < n) wv[r] = w[i];
-      else if constexpr (kC) { wv[r].x = 0; wv[r].y = 0; } else wv[r] = 0;
-    }
-    for (int k = 0; k < S.m; k++) {
-      const V *u = vec<V>(S, k);
-      double re = 0.0, im = 0.0;
+  for (int q = 0; q < kGroup; q++) { re[q] = im[q] = 0.0; rh[q] = rl[q] = ih[q] = il[q] = 0.f; }
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const V wv = w[i];
 #pragma unroll
-      for (int r = 0; r < kRows; r++) {
-        const int64_t i = r0 + 32 * r;
-        if (i < n) {
-          const V a = u[i];
-          if constexpr (kC) {   // conj(a) * w
-            re += (double)a.x * wv[r].x + (double)a.y * wv[r].y;
-            im += (double)a.x * wv[r].y - (double)a.y * wv[r].x;
-          } else {
-            re += (double)a * (double)wv[r];
-          }
+    for (int q = 0; q < kGroup; q++) {
+      if (q < kn) {
+        const V a = vec<V>(S, k0 + q)[i];
+        if constexpr (kF && kC) {          // conj(a) * w
+          df_add_prod(rh[q], rl[q], a.x, wv.x);
+          df_add_prod(rh[q], rl[q], a.y, wv.y);
+          df_add_prod(ih[q], il[q], a.x, wv.y);
+          df_add_prod(ih[q], il[q], -a.y, wv.x);
+        } else if constexpr (kF) {
+          df_add_prod(rh[q], rl[q], a, wv);
+        } else if constexpr (kC) {
+          re[q] += a.x * wv.x + a.y * wv.y;
+          im[q] += a.x * wv.y - a.y * wv.x;
+        } else {
+          re[q] += a * wv;
         }
-      }
-      re = warp_sum(re);
-      if constexpr (kC) im = warp_sum(im);
-      if (lane == 0) {
-        acc[(k * P) * kWarps + wid] += re;
-        if constexpr (kC) acc[(k * P + 1) * kWarps + wid] += im;
       }
     }
   }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kGroup; q++) {
+    double a0 = re[q], b0 = im[q];
+    if constexpr (kF) { a0 = df_value(rh[q], rl[q]); b0 = df_value(ih[q], il[q]); }
+    const double a = warp_sum(a0);
+    double b = 0.0;
+    if constexpr (kC) b = warp_sum(b0);
+    if (lane == 0) {
+      red[q * P][wid] = a;
+      if constexpr (kC) red[q * P + 1][wid] = b;
+    }
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < S.m * P; t += kThreads) {
-    double s = 0.0;
-    for (int q = 0; q < kWarps; q++) s += acc[t * kWarps + q];
-    partial[(size_t)t * gridDim.x + blockIdx.x] = s;
+  if (threadIdx.x < kn * P) {
+    double sacc = 0.0;
+    for (int q = 0; q < kWarps; q++) sacc += red[threadIdx.x][q];
+    partial[(size_t)(k0 * P + threadIdx.x) * gridDim.x + blockIdx.x] = sacc;
   }
 }
 
@@ -134,40 +147,75 @@ __device__ __forceinline__ void block_sum_store(double d, double *out, int slot)
   }
 }
 
-// w <- w - sum_k c_k u_k in fp64, rounded once; partial[blk] = the block's ||w||^2.
+// w <- w - sum_k c_k u_k, rounded once; partial[blk] = the block's ||w||^2.  fp32 vectors:
+// every coefficient split into two fp32 words and the sum carried in double-float; fp64
+// vectors: fp64.
 template <typename V>
 __global__ void __launch_bounds__(kThreads) update_kernel(VecSet S, const double *c, V *w,
                                                           int64_t n, double *partial) {
   using A = typename Rv<V>::A;
   constexpr bool kC = Rv<V>::cplx;
-  extern __shared__ double cs[];   // [m][P]
-  const int P = kC ? 2 : 1;
-  for (int t = threadIdx.x; t < S.m * P; t += kThreads) cs[t] = c[t];
+  constexpr bool kF = std::is_same<A, float>::value;
+  constexpr int P = kC ? 2 : 1;
+  extern __shared__ double cs[];   // [m][P] fp64, then (fp32 vectors) [m][P][2] words
+  float *cf = reinterpret_cast<float *>(cs + S.m * P);
+  for (int t = threadIdx.x; t < S.m * P; t += kThreads) {
+    cs[t] = c[t];
+    if constexpr (kF) df_split(c[t], cf[2 * t], cf[2 * t + 1]);
+  }
   __syncthreads();
+  float nh = 0.f, nl = 0.f;
   double nrm = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
-    if constexpr (kC) {
+    if constexpr (kF && kC) {
+      const V w0 = w[i];
+      float rh = w0.x, rl = 0.f, ih = w0.y, il = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < S.m; k++) {
+        const V a = vec<V>(S, k)[i];
+        const float crh = cf[4 * k], crl = cf[4 * k + 1], cih = cf[4 * k + 2], cil = cf[4 * k + 3];
+        df_sub_scaled(rh, rl, crh, crl, a.x);     // - cr a.x
+        df_sub_scaled(rh, rl, -cih, -cil, a.y);   // + ci a.y
+        df_sub_scaled(ih, il, crh, crl, a.y);     // - cr a.y
+        df_sub_scaled(ih, il, cih, cil, a.x);     // - ci a.x
+      }
+      V o;
+      o.x = df_round(rh, rl);
+      o.y = df_round(ih, il);
+      w[i] = o;
+      df_add_prod(nh, nl, o.x, o.x);
+      df_add_prod(nh, nl, o.y, o.y);
+    } else if constexpr (kF) {
+      float hi = w[i], lo = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < S.m; k++) df_sub_scaled(hi, lo, cf[2 * k], cf[2 * k + 1], vec<V>(S, k)[i]);
+      const float o = df_round(hi, lo);
+      w[i] = o;
+      df_add_prod(nh, nl, o, o);
+    } else if constexpr (kC) {
       double wr = w[i].x, wi = w[i].y;
+#pragma unroll 4
       for (int k = 0; k < S.m; k++) {
         const V a = vec<V>(S, k)[i];
         const double cr = cs[2 * k], ci = cs[2 * k + 1];
-        wr -= cr * (double)a.x - ci * (double)a.y;
-        wi -= cr * (double)a.y + ci * (double)a.x;
+        wr -= cr * a.x - ci * a.y;
+        wi -= cr * a.y + ci * a.x;
       }
       V o;
-      o.x = (A)wr;
-      o.y = (A)wi;
+      o.x = wr;
+      o.y = wi;
       w[i] = o;
-      nrm += (double)o.x * o.x + (double)o.y * o.y;
+      nrm += wr * wr + wi * wi;
     } else {
-      double t = (double)w[i];
-      for (int k = 0; k < S.m; k++) t -= cs[k] * (double)vec<V>(S, k)[i];
-      const A o = (A)t;
-      w[i] = o;
-      nrm += (double)o * (double)o;
+      double t = w[i];
+#pragma unroll 8
+      for (int k = 0; k < S.m; k++) t -= cs[k] * vec<V>(S, k)[i];
+      w[i] = t;
+      nrm += t * t;
     }
   }
+  if constexpr (kF) nrm = df_value(nh, nl);
   block_sum_store(nrm, partial, blockIdx.x);
 }
 
@@ -177,26 +225,46 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(VecSet S, const doubl
                                                            int64_t n) {
   using A = typename Rv<V>::A;
   constexpr bool kC = Rv<V>::cplx;
+  constexpr bool kF = std::is_same<A, float>::value;
   extern __shared__ double cs[];
-  for (int t = threadIdx.x; t < S.m; t += kThreads) cs[t] = s[t];
+  float *cf = reinterpret_cast<float *>(cs + S.m);
+  for (int t = threadIdx.x; t < S.m; t += kThreads) {
+    cs[t] = s[t];
+    if constexpr (kF) df_split(s[t], cf[2 * t], cf[2 * t + 1]);
+  }
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
-    if constexpr (kC) {
+    if constexpr (kF && kC) {
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      for (int k = 0; k < S.m; k++) {
+        const V a = vec<V>(S, k)[i];
+        df_sub_scaled(rh, rl, -cf[2 * k], -cf[2 * k + 1], a.x);
+        df_sub_scaled(ih, il, -cf[2 * k], -cf[2 * k + 1], a.y);
+      }
+      V o;
+      o.x = df_round(rh, rl);
+      o.y = df_round(ih, il);
+      psi[i] = o;
+    } else if constexpr (kF) {
+      float hi = 0.f, lo = 0.f;
+      for (int k = 0; k < S.m; k++) df_sub_scaled(hi, lo, -cf[2 * k], -cf[2 * k + 1], vec<V>(S, k)[i]);
+      psi[i] = df_round(hi, lo);
+    } else if constexpr (kC) {
       double re = 0.0, im = 0.0;
       for (int k = 0; k < S.m; k++) {
         const V a = vec<V>(S, k)[i];
-        re += cs[k] * (double)a.x;
-        im += cs[k] * (double)a.y;
+        re += cs[k] * a.x;
+        im += cs[k] * a.y;
       }
       V o;
-      o.x = (A)re;
-      o.y = (A)im;
+      o.x = re;
+      o.y = im;
       psi[i] = o;
     } else {
       double t = 0.0;
-      for (int k = 0; k < S.m; k++) t += cs[k] * (double)vec<V>(S, k)[i];
-      psi[i] = (A)t;
+      for (int k = 0; k < S.m; k++) t += cs[k] * vec<V>(S, k)[i];
+      psi[i] = t;
     }
   }
 }
@@ -235,14 +303,11 @@ int ed_launch_reorth_sweep(const ed_basis *B, void *w, const void *base, const v
   const int P = cplx ? 2 : 1;
   const int grid = ed_reorth_grid(B);
   const VecSet S = make_set(base, B->D, p0, p1, m);
-  const size_t smem_dot = sizeof(double) * (size_t)m * P * kWarps;
-  const size_t smem_upd = sizeof(double) * (size_t)m * P;
-  if (smem_dot > 200 * 1024) return ed_fail(ED_ERR_UNSUPPORTED, "too many vectors in one sweep");
+  const size_t smem_upd = 2 * sizeof(double) * (size_t)m * P;   // fp64 + two fp32 words
+  if (smem_upd > 48 * 1024) return ed_fail(ED_ERR_UNSUPPORTED, "too many vectors in one sweep");
+  const dim3 dgrid(grid, (m + kGroup - 1) / kGroup);
   RO_DISPATCH(dtype, {
-    auto kd = multidot_kernel<V>;
-    if (smem_dot > 48 * 1024)
-      ED_CK(cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dot));
-    kd<<<grid, kThreads, smem_dot, st>>>(S, (const V *)w, B->D, partial);
+    multidot_kernel<V><<<dgrid, kThreads, 0, st>>>(S, (const V *)w, B->D, partial);
     ED_CK(cudaGetLastError());
     coef_kernel<<<m * P, kThreads, 0, st>>>(partial, grid, c);
     ED_CK(cudaGetLastError());
@@ -256,7 +321,7 @@ int ed_launch_reorth_sweep(const ed_basis *B, void *w, const void *base, const v
 int ed_launch_combine(const ed_basis *B, void *psi, const void *base, int m, const double *s,
                       int dtype, cudaStream_t st) {
   const VecSet S = make_set(base, B->D, nullptr, nullptr, m);
-  const size_t smem = sizeof(double) * (size_t)m;
+  const size_t smem = 2 * sizeof(double) * (size_t)m;
   if (smem > 200 * 1024) return ed_fail(ED_ERR_UNSUPPORTED, "too many vectors to combine");
   RO_DISPATCH(dtype, {
     auto k = combine_kernel<V>;

@@ -269,6 +269,8 @@ struct ed_basis {
   std::vector<uint8_t> bond_pad;       // bonds padded per class to words of 32 (inert (0,0))
   std::vector<int32_t> cls_word;       // [n_classes+1] word ranges per class
   std::vector<uint32_t> bond_blk;      // padded bonds: block | block << 4 | bit << 8 | bit << 16
+  int n_nib = 0;                       // 4-bit nibbles of a state, (N + 3) / 4
+  std::vector<uint32_t> nib;           // [word][nibble][16]: antiparallel-mask contributions
   // tables
   DevTables T{};
   uint32_t *d_rep = nullptr, *d_sym_off = nullptr;
@@ -284,6 +286,7 @@ struct ed_basis {
   uint16_t *d_list2 = nullptr;
   uint8_t *d_bond_pad = nullptr;
   uint32_t *d_bond_blk = nullptr;
+  uint32_t *d_nib = nullptr;
   int32_t *d_phase = nullptr;
   std::shared_ptr<uint64_t> full_tab;  // one-sublattice table, shareable between sectors
   uint8_t *d_pbit = nullptr;
@@ -298,6 +301,10 @@ struct ed_basis {
   uint32_t *d_top_rank = nullptr, *d_limits = nullptr;
   void *d_postfix = nullptr;
   int64_t n_keys = 0, max_bucket = 0;
+  // ranked Limits: per key {first index, 0, 64-bit bitmap of the postfixes present}
+  void *d_rlim = nullptr;
+  int rq_bits = 0, rpost_bits = 0;
+  int64_t n_rkeys = 0;
   size_t index_bytes = 0;
   // per-class bond data and norm tables for apply_H
   double *d_sqrt = nullptr, *d_rsqrt = nullptr;   // [nsym+1]

@@ -21,8 +21,10 @@ def test_row_partition_covers_and_balances():
         assert parts[0][0] == 0 and parts[-1][1] == D
         assert all(a <= b for a, b in parts)
         assert all(parts[r][1] == parts[r + 1][0] for r in range(world - 1))
-        sizes = [b - a for a, b in parts]
-        assert max(sizes) - min(sizes) <= 1
+        # blocks of ceil(D / world) rows back to back, so the gathered slices need no
+        # reordering: every block starts at r * m
+        m = -(-D // world) if D else 0
+        assert all(a == min(r * m, D) and b - a <= m for r, (a, b) in enumerate(parts))
     w = np.r_[np.full(50, 10.0), np.ones(50)]
     parts = row_partition(100, 2, w)
     loads = [w[a:b].sum() for a, b in parts]
@@ -57,6 +59,12 @@ def _worker(rank, world, port, out):
         x = w.state_uniform(bs, 1804) + 1j * w.state_uniform(bs, 1805)
         y_local = op.matvec(torch.from_numpy(x[op.r0:op.r1]))
         ok_mv = np.abs(y_local.numpy() - (Hc @ x)[op.r0:op.r1]).max() < 1e-13
+        # a weighted partition (uneven slices, gathered through a reordering copy)
+        wts = np.linspace(1.0, 5.0, bs.size)
+        opw = ShardedOperator(local_apply, bs.size, rank, world, weights=wts)
+        for _ in range(2):         # the preallocated buffers are reused
+            y_w = opw.matvec(torch.from_numpy(x[opw.r0:opw.r1]))
+            ok_mv = ok_mv and np.abs(y_w.numpy() - (Hc @ x)[opw.r0:opw.r1]).max() < 1e-13
         v0 = torch.from_numpy(x[op.r0:op.r1].copy())
         e, steps, a, b = sharded_lanczos(op, v0)
         e_ref = np.linalg.eigvalsh(H.toarray())[0]
