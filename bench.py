@@ -370,7 +370,8 @@ def bench_sector(ed, torch, workload, p, steps, warmup, ctx, accuracy=True, full
     n_sm = ctx["n_sm"]
     results = {}
     for name, dt, vb in (("f64", torch.float64, 8), ("mixed", torch.float32, 4)):
-        work = torch.empty(3 * D, dtype=dt, device="cuda")
+        # three Lanczos vectors; with fp32 a fourth for the low words of the product
+        work = torch.empty((3 if name == "f64" else 4) * D, dtype=dt, device="cuda")
         B.lanczos(dtype=dt, fixed_steps=max(warmup, 1), work=work)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -224,7 +224,10 @@ typedef struct {
   double *beta;               /* optional HOST output of M doubles (M as for alpha) */
   void *stream;
   void *work;                 /* optional DEVICE workspace of >= 3 * dim elements of dtype,
-                                 caller-owned; when NULL the call allocates its own */
+                                 caller-owned; when NULL the call allocates its own.  With
+                                 fp32 vectors a fourth dim-element slice, when the workspace
+                                 holds one, keeps the low words of the product (y as a
+                                 double-float pair); otherwise the call allocates it */
   int64_t work_bytes;         /* size of work in bytes */
   double tol_residual;        /* > 0: also require the Ritz residual beta_m |s_m| of the lowest
                                  pair to fall below tol_residual * max(1, |E0|) (for an
@@ -255,8 +258,10 @@ typedef struct {
  * matrix-vector product (Sec. IV: the product dominates; dots, scalings and the
  * tridiagonal eigenproblem are cheap).  Three device vectors of dtype (four with psi),
  * or the caller's Krylov store with ED_REORTH_FULL; alpha = <v, Hv> and beta = ||w||
- * reduced in double per block then summed on the host in a fixed order; the
- * reorthogonalisation chosen by opts->reorth (default: a second sweep against the last
+ * reduced in double per block then summed on the host in a fixed order (with fp32
+ * vectors the product y is kept to about 48 bits -- fp32 value plus its rounding
+ * remainder -- until the three-term update has used it, so that only the stored vectors
+ * are rounded to fp32); the reorthogonalisation chosen by opts->reorth (default: a second sweep against the last
  * two vectors), with alpha_j corrected by the sweeps' <v_j, w>; lowest eigenvalue of the
  * tridiagonal matrix by Sturm-sequence bisection in double.  With psi and without a
  * Krylov store the ground state comes from a second pass of the same recurrence

@@ -270,7 +270,7 @@ __global__ void dot_kernel(const V *x, const V *y, int64_t n, double *partial) {
 // this GPU is too slow for a pass over the whole vector.
 template <typename V>
 __global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, double b,
-                                 int64_t n, double *partial) {
+                                 int64_t n, double *partial, const V *wlo) {
   using A = typename Vt<V>::A;
   constexpr bool kF = sizeof(A) == 4;
   double acc = 0;
@@ -285,6 +285,7 @@ __global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, dou
       // a and b are real (Hermitian tridiagonal)
       const V w0 = w[i], v0 = v[i];
       float rh = w0.x, rl = 0.f, ih = w0.y, il = 0.f;
+      if (wlo) { const V l0 = wlo[i]; rl = l0.x; il = l0.y; }
       df_sub_scaled(rh, rl, ah, al, v0.x);
       df_sub_scaled(ih, il, ah, al, v0.y);
       if (vprev) {
@@ -297,7 +298,7 @@ __global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, dou
       df_add_prod(nh, nl, o.x, o.x);
       df_add_prod(nh, nl, o.y, o.y);
     } else if constexpr (kF) {
-      float hi = w[i], lo = 0.f;
+      float hi = w[i], lo = wlo ? wlo[i] : 0.f;
       df_sub_scaled(hi, lo, ah, al, v[i]);
       if (vprev) df_sub_scaled(hi, lo, bh, bl, vprev[i]);
       const float o = df_round(hi, lo);
@@ -377,12 +378,18 @@ static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const void *x,
                     void *y, int dtype, int64_t r0, int64_t r1, double *partial,
-                    cudaStream_t st, int mode) {
+                    cudaStream_t st, int mode, void *ylo) {
   if (r1 <= r0) return ED_OK;
   if (!getenv("SCED_GENERIC_APPLY")) {
-    const int rc = ed_launch_apply_fast(B, J, Jz, x, y, dtype, r0, r1, partial, st, mode);
-    if (rc != ED_ERR_UNSUPPORTED) return rc;
+    bool done = false;
+    const int rc = ed_launch_apply_fast(B, J, Jz, x, y, dtype, r0, r1, partial, st, mode, ylo, &done);
+    if (rc != ED_ERR_UNSUPPORTED) {
+      if (!rc && ylo && !done)
+        ED_CK(cudaMemsetAsync(ylo, 0, (size_t)(r1 - r0) * (dtype == ED_C64 ? 8 : 4), st));
+      return rc;
+    }
   }
+  if (ylo) ED_CK(cudaMemsetAsync(ylo, 0, (size_t)(r1 - r0) * (dtype == ED_C64 ? 8 : 4), st));
   ApplyParams P{};
   P.T = B->T;
   P.I = B->I;
@@ -487,10 +494,11 @@ int ed_launch_dot(const ed_basis *B, const void *x, const void *y, int dtype, do
 }
 
 int ed_launch_axpy_norm(const ed_basis *B, void *w, const void *v, const void *vprev, double a,
-                        double b, int dtype, double *partial, int nblk, cudaStream_t st) {
+                        double b, int dtype, double *partial, int nblk, cudaStream_t st,
+                        const void *wlo) {
   ED_DISPATCH(dtype, (axpy_norm_kernel<V><<<nblk, 256, 0, st>>>((V *)w, (const V *)v,
                                                                 (const V *)vprev, a, b, B->D,
-                                                                partial)));
+                                                                partial, (const V *)wlo)));
   ED_CK(cudaGetLastError());
   return ED_OK;
 }

@@ -21,6 +21,7 @@
 // the representative: prefix rank, Limits bucket, binary search of the narrow postfixes.  fp32 vectors are summed per row with a compensated
 // (two-float) accumulator, fp64 in fp64.  Each y_i written once; no atomics.
 #include "sced_internal.cuh"
+#include "dfloat.cuh"
 #include <algorithm>
 #include <cstdlib>
 #include <type_traits>
@@ -55,12 +56,13 @@ struct TwoParams {
   int64_t D;
   const void *x;
   void *y;
+  void *ylo;                     // fp32 vectors: optional low words of y (double-float y)
   int64_t r0, r1;
   double *partial;
   uint32_t n_e1, n_e2, n_rid, n_dest, n_bond, n_top, n_sq, n_cs;
   uint32_t off_bblk, off_e2, off_e1, off_rid, off_dest, off_src, off_phase, off_bond, off_top, off_sq, off_cs,
       smem_bytes;
-  // term-parallel kernel: fp32 norm / character tables and the per-warp row states and
+  // term-parallel kernel: fp32 weight / character tables and the per-warp row states and
   // term lists (0 when the layout has no tile region)
   uint32_t off_sqf, off_csf, off_tile, tile_warps;
   const uint32_t *nib;           // antiparallel masks by nibbles, [word][n_nib][16]
@@ -80,8 +82,8 @@ struct Sm2 {
 };
 
 // per-warp shared memory of the term-parallel kernel: 32 row states, 32 row accumulators
-// (real and imaginary parts), then a list of at most 32 x 16 terms of 16 bits
-constexpr uint32_t kTileWarpBytes = 32 * 8 + 32 * 8 + 32 * 16 * 2;
+// (real and imaginary parts, up to fp64), then a list of at most 32 x 16 terms of 16 bits
+constexpr uint32_t kTileWarpBytes = 32 * 8 + 32 * 16 + 32 * 16 * 2;
 
 struct Rep2 {
   uint32_t minrep;   // top block of the representative
@@ -569,12 +571,25 @@ __device__ __forceinline__ bool find_rep_simple(const Sm2 &S, const TwoParams &P
 // the lane holding a segment's last term adds the sum to the row's shared accumulator.
 // Every step has a fixed order, so the product is deterministic; no atomics.
 // ---------------------------------------------------------------------------------------
+// weights of the term-parallel kernel (shared memory): fp32 vectors use, per coupling
+// class c and stabiliser order t, J_c / 2 sqrt(t) split into two fp32 words, and for
+// complex sectors (cos, remainder, sin, remainder) per character; fp64 vectors use the
+// fp64 tables
+struct TileW {
+  const float2 *wf;
+  const float4 *csf4;
+  const double *sqd, *csd;
+  int n_sq;
+};
+
 template <typename V, int NSUB, bool kE2, bool kGeneral>
 __device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, const V *x,
-                                           const float *sqf, const float *csf,
-                                           const uint64_t *rowst, uint16_t *list, int base,
-                                           int T, int bbase, float jhc, float *racc, int *n_def) {
+                                           const TileW &W, int c, const uint64_t *rowst,
+                                           uint16_t *list, int base, int T, int bbase,
+                                           double *racc, int *n_def) {
+  using A = typename Vf<V>::A;
   constexpr bool kC = Vf<V>::cplx;
+  constexpr bool kF = sizeof(A) == 4;
   const unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31;
   const int N = P.N, n = P.n;
@@ -583,7 +598,8 @@ __device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, con
   int r = 32;
   uint32_t e = 0;
   bool defer = false;
-  float v_re = 0.f, v_im = 0.f;
+  A v_re = 0, v_im = 0;
+  float l_re = 0.f, l_im = 0.f;   // fp32 vectors: low words of the values (double-float)
   if (t < T) {
     e = list[t];
     r = (int)(e >> 5);
@@ -608,14 +624,33 @@ __device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, con
       const int64_t j = P.rlim ? lookup_ranked(S, P, R.minrep, R.low) : lookup_two(S, P, R.minrep, R.low);
       if (j >= 0) {
         const V xj = gather_x(x, j);
-        const float wgt = R.t == 1 ? jhc : jhc * sqf[R.t];   // J_c / 2 sqrt(|Stab_j|)
-        if constexpr (!kC) {
-          const float pv = wgt * xj;
-          v_re = R.ph == 0 ? pv : -pv;
+        if constexpr (kF) {
+          // the weight J_c / 2 sqrt(|Stab_j|) as two fp32 words, so that no rounding of it
+          // is repeated in every term with the same class and stabiliser order (a bias
+          // that would not average out over the sector)
+          const float2 wv = W.wf[c * W.n_sq + R.t];
+          if constexpr (!kC) {   // (wh + wl) xj as an unevaluated pair
+            const float ph_ = __fmul_rn(wv.x, xj);
+            const float pl_ = __fmaf_rn(wv.y, xj, __fmaf_rn(wv.x, xj, -ph_));
+            v_re = R.ph == 0 ? ph_ : -ph_;
+            l_re = R.ph == 0 ? pl_ : -pl_;
+          } else {
+            const float4 cs = W.csf4[R.ph];   // cos, its remainder, sin, its remainder
+            const float crh = wv.x * cs.x, crl = fmaf(wv.x, cs.x, -crh) + fmaf(wv.x, cs.y, wv.y * cs.x);
+            const float cih = wv.x * cs.z, cil = fmaf(wv.x, cs.z, -cih) + fmaf(wv.x, cs.w, wv.y * cs.z);
+            v_re = fmaf(crh, xj.x, fmaf(crl, xj.x, -fmaf(cih, xj.y, cil * xj.y)));
+            v_im = fmaf(crh, xj.y, fmaf(crl, xj.y, fmaf(cih, xj.x, cil * xj.x)));
+          }
         } else {
-          const float cr = csf[2 * R.ph] * wgt, ci = csf[2 * R.ph + 1] * wgt;
-          v_re = cr * xj.x - ci * xj.y;
-          v_im = cr * xj.y + ci * xj.x;
+          const double wgt = P.jh[c] * W.sqd[R.t];   // J_c / 2 sqrt(|Stab_j|)
+          if constexpr (!kC) {
+            const double pv = wgt * xj;
+            v_re = R.ph == 0 ? pv : -pv;
+          } else {
+            const double cr = W.csd[2 * R.ph] * wgt, ci = W.csd[2 * R.ph + 1] * wgt;
+            v_re = cr * xj.x - ci * xj.y;
+            v_im = cr * xj.y + ci * xj.x;
+          }
         }
       }
     }
@@ -627,23 +662,38 @@ __device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, con
     if (defer) list[*n_def + __popc(dm & ((1u << lane) - 1u))] = (uint16_t)e;
     *n_def += __popc(dm);
   }
-  // segmented inclusive scan: lanes with the same row form one segment
+  // segmented inclusive scan: lanes with the same row form one segment (fp32 values are
+  // summed in double-float, so the sum of a segment carries no fp32 rounding)
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int ru = __shfl_up_sync(FULL, r, d);
-    const float a = __shfl_up_sync(FULL, v_re, d);
-    float b = 0.f;
+    const A a = __shfl_up_sync(FULL, v_re, d);
+    A b = 0;
     if constexpr (kC) b = __shfl_up_sync(FULL, v_im, d);
+    float al = 0.f, bl = 0.f;
+    if constexpr (kF) {
+      al = __shfl_up_sync(FULL, l_re, d);
+      if constexpr (kC) bl = __shfl_up_sync(FULL, l_im, d);
+    }
     if (lane >= d && ru == r) {
-      v_re += a;
-      if constexpr (kC) v_im += b;
+      if constexpr (kF) {
+        df_add(v_re, l_re, a);
+        l_re = __fadd_rn(l_re, al);
+        if constexpr (kC) {
+          df_add(v_im, l_im, b);
+          l_im = __fadd_rn(l_im, bl);
+        }
+      } else {
+        v_re += a;
+        if constexpr (kC) v_im += b;
+      }
     }
   }
   const int rn = __shfl_down_sync(FULL, r, 1);
   __syncwarp();   // the previous round's accumulator updates are visible
   if (r < 32 && (lane == 31 || rn != r)) {   // last lane of its segment
-    racc[r] += v_re;
-    if constexpr (kC) racc[32 + r] += v_im;
+    racc[r] += (double)v_re + (double)l_re;
+    if constexpr (kC) racc[32 + r] += (double)v_im + (double)l_im;
   }
 }
 
@@ -656,24 +706,39 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
   {
     const double *sqd = reinterpret_cast<const double *>(sm + P.off_sq);
     const double *csd = reinterpret_cast<const double *>(sm + P.off_cs);
-    float *sqf = reinterpret_cast<float *>(sm + P.off_sqf);
-    float *csf = reinterpret_cast<float *>(sm + P.off_csf);
-    for (uint32_t k = threadIdx.x; k < P.n_sq; k += blockDim.x) sqf[k] = (float)sqd[k];
-    if (kC) for (uint32_t k = threadIdx.x; k < P.n_cs; k += blockDim.x) csf[k] = (float)csd[k];
+    float2 *wf = reinterpret_cast<float2 *>(sm + P.off_sqf);
+    float4 *csf4 = reinterpret_cast<float4 *>(sm + P.off_csf);
+    for (uint32_t k = threadIdx.x; k < (uint32_t)P.n_classes * P.n_sq; k += blockDim.x) {
+      const double wv = P.jh[k / P.n_sq] * sqd[k % P.n_sq];
+      const float hi = (float)wv;
+      wf[k] = make_float2(hi, (float)(wv - (double)hi));
+    }
+    if (kC)
+      for (uint32_t k = threadIdx.x; k < P.n_cs / 2; k += blockDim.x) {
+        const double cv = csd[2 * k], sv = csd[2 * k + 1];
+        const float ch = (float)cv, sh = (float)sv;
+        csf4[k] = make_float4(ch, (float)(cv - (double)ch), sh, (float)(sv - (double)sh));
+      }
     uint32_t *nb = reinterpret_cast<uint32_t *>(sm + P.off_nib);
     const uint32_t n_nibtab = (uint32_t)P.cls_word[P.n_classes] * P.n_nib * 16;
     for (uint32_t k = threadIdx.x; k < n_nibtab; k += blockDim.x) nb[k] = P.nib[k];
     __syncthreads();
   }
   const uint32_t *nibs = reinterpret_cast<const uint32_t *>(sm + P.off_nib);
-  const float *sqf = reinterpret_cast<const float *>(sm + P.off_sqf);
-  const float *csf = reinterpret_cast<const float *>(sm + P.off_csf);
+  TileW W;
+  W.wf = reinterpret_cast<const float2 *>(sm + P.off_sqf);
+  W.csf4 = reinterpret_cast<const float4 *>(sm + P.off_csf);
+  W.sqd = reinterpret_cast<const double *>(sm + P.off_sq);
+  W.csd = reinterpret_cast<const double *>(sm + P.off_cs);
+  W.n_sq = (int)P.n_sq;
+  using A = typename Vf<V>::A;
+  constexpr bool kF = sizeof(A) == 4;
   const double *rsd = reinterpret_cast<const double *>(sm + P.off_sq) + P.n_sq;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned char *tw = sm + P.off_tile + (size_t)wid * kTileWarpBytes;
   uint64_t *rowst = reinterpret_cast<uint64_t *>(tw);
-  float *racc = reinterpret_cast<float *>(tw + 32 * 8);            // [2][32] re, im
-  uint16_t *list = reinterpret_cast<uint16_t *>(tw + 32 * 8 + 32 * 8);
+  double *racc = reinterpret_cast<double *>(tw + 32 * 8);          // [2][32] re, im
+  uint16_t *list = reinterpret_cast<uint16_t *>(tw + 32 * 8 + 32 * 16);
   const V *x = reinterpret_cast<const V *>(P.x);
   V *y = reinterpret_cast<V *>(P.y);
   const unsigned FULL = 0xFFFFFFFFu;
@@ -684,13 +749,12 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
     {
       const int64_t i = P.r0 + (tile << 5) + lane;
       rowst[lane] = i < P.r1 ? __ldcs(reinterpret_cast<const unsigned long long *>(P.basis) + i) : 0ULL;
-      racc[lane] = 0.f;
-      if (kC) racc[32 + lane] = 0.f;
+      racc[lane] = 0.0;
+      if (kC) racc[32 + lane] = 0.0;
     }
     const bool valid = P.r0 + (tile << 5) + lane < P.r1;
     double diag = 0.0;
     for (int c = 0; c < P.n_classes; c++) {
-      const float jhc = (float)P.jh[c];
       int nanti = 0;
       for (int wd = P.cls_word[c]; wd < P.cls_word[c + 1]; wd++) {
         uint32_t m = 0;
@@ -726,10 +790,10 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
           const int bbase = wd * 32 + kTileChunk * h;
           int n_def = 0;
           for (int base = 0; base < T; base += 32)
-            tile_round<V, NSUB, kE2, false>(S, P, x, sqf, csf, rowst, list, base, T, bbase, jhc, racc, &n_def);
+            tile_round<V, NSUB, kE2, false>(S, P, x, W, c, rowst, list, base, T, bbase, racc, &n_def);
           __syncwarp();
           for (int base = 0; base < n_def; base += 32)
-            tile_round<V, NSUB, kE2, true>(S, P, x, sqf, csf, rowst, list, base, n_def, bbase, jhc, racc, &n_def);
+            tile_round<V, NSUB, kE2, true>(S, P, x, W, c, rowst, list, base, n_def, bbase, racc, &n_def);
           __syncwarp();   // the list is rewritten by the next chunk
         }
       }
@@ -740,21 +804,37 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
       const int64_t i = P.r0 + (tile << 5) + lane;
       const double rs = rsd[__ldcs(P.stab + i)];
       const double row_re = (double)racc[lane];
+      // y_i in fp64, rounded once to the vector type; for fp32 vectors the rounding's
+      // remainder goes to ylo when asked (the mixed Lanczos keeps y as a double-float
+      // pair for its update), and <x, y> uses the unrounded value
       if constexpr (!kC) {
         const double xi = (double)x[i];
-        const float yi = (float)(diag * xi + row_re * rs);
+        const double yd = diag * xi + row_re * rs;
+        const A yi = (A)yd;
         __stcs(y + (i - P.r0), yi);
-        if (P.partial) dot_re += xi * (double)yi;
+        if (kF && P.ylo) reinterpret_cast<float *>(P.ylo)[i - P.r0] = (float)(yd - (double)yi);
+        if (P.partial) dot_re += xi * (kF && P.ylo ? yd : (double)yi);
       } else {
         const double row_im = (double)racc[32 + lane];
         const V xv = x[i];
+        const double yr = diag * (double)xv.x + row_re * rs;
+        const double yim = diag * (double)xv.y + row_im * rs;
         V yv;
-        yv.x = (float)(diag * (double)xv.x + row_re * rs);
-        yv.y = (float)(diag * (double)xv.y + row_im * rs);
+        yv.x = (A)yr;
+        yv.y = (A)yim;
         y[i - P.r0] = yv;
+        double ur = (double)yv.x, ui = (double)yv.y;
+        if (kF && P.ylo) {
+          float2 lo;
+          lo.x = (float)(yr - ur);
+          lo.y = (float)(yim - ui);
+          reinterpret_cast<float2 *>(P.ylo)[i - P.r0] = lo;
+          ur = yr;
+          ui = yim;
+        }
         if (P.partial) {
-          dot_re += (double)xv.x * yv.x + (double)xv.y * yv.y;
-          dot_im += (double)xv.x * yv.y - (double)xv.y * yv.x;
+          dot_re += (double)xv.x * ur + (double)xv.y * ui;
+          dot_im += (double)xv.x * ui - (double)xv.y * ur;
         }
       }
     }
@@ -861,8 +941,8 @@ int make_params(const ed_basis *B, const double *J, const double *Jz, bool e2, T
   P.nib = B->d_nib;
   P.n_nib = (uint32_t)B->n_nib;
   if (tile_warps) {
-    put(P.off_sqf, 4 * (size_t)P.n_sq);
-    put(P.off_csf, 4 * (size_t)P.n_cs);
+    put(P.off_sqf, 8 * (size_t)P.n_sq * B->n_classes);   // J_c/2 sqrt(t) as float2
+    put(P.off_csf, 8 * (size_t)P.n_cs);                  // (cos, rem, sin, rem) as float4
     put(P.off_nib, 4 * B->nib.size());
     put(P.off_tile, (size_t)tile_warps * kTileWarpBytes);
   }
@@ -938,15 +1018,15 @@ int launch_tile_v(const TwoParams &P, bool e2, int nsub, int grid, cudaStream_t 
 // |G| <= 4096); returns ED_ERR_UNSUPPORTED otherwise (the caller uses the generic kernel).
 int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
                          void *y, int dtype, int64_t r0, int64_t r1, double *partial,
-                         cudaStream_t st, int mode) {
+                         cudaStream_t st, int mode, void *ylo, bool *ylo_done) {
   TwoParams P;
   bool e2 = true;
   int rc = make_params(B, J, Jz, e2, P);
   if (rc == ED_ERR_UNSUPPORTED) { e2 = false; rc = make_params(B, J, Jz, false, P); }
   if (rc) return rc;
-  // fp32 vectors: the term-parallel kernel (level-2 tables staged when they fit with the
+  // the product: the term-parallel kernel (level-2 tables staged when they fit with the
   // per-warp term lists, else read from global memory)
-  if (mode == 0 && (dtype == ED_F32 || dtype == ED_C64) && !getenv("SCED_ROW_KERNEL")) {
+  if (mode == 0 && !getenv("SCED_ROW_KERNEL")) {
     TwoParams Q;
     bool qe2 = e2;
     int qrc = make_params(B, J, Jz, qe2, Q, (qe2 ? kTileThreadsE2 : kTileThreads) / 32);
@@ -956,6 +1036,8 @@ int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, c
     }
     if (qrc == ED_OK) {
       Q.x = x; Q.y = y; Q.r0 = r0; Q.r1 = r1; Q.partial = partial;
+      Q.ylo = (dtype == ED_F32 || dtype == ED_C64) ? ylo : nullptr;
+      if (ylo_done) *ylo_done = Q.ylo != nullptr;
       const int bs = qe2 ? kTileThreadsE2 : kTileThreads;
       int grid = B->sm_count * (qe2 ? 1 : kTileMinBlocks);
       const int64_t need = (r1 - r0 + bs - 1) / bs;
@@ -963,8 +1045,13 @@ int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, c
       if (grid < 1) grid = 1;
       if (partial && grid > B->n_partial / 2) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
       B->last_apply_grid = grid;
-      return dtype == ED_F32 ? launch_tile_v<float>(Q, qe2, B->nsub, grid, st)
-                             : launch_tile_v<float2>(Q, qe2, B->nsub, grid, st);
+      switch (dtype) {
+        case ED_F32: return launch_tile_v<float>(Q, qe2, B->nsub, grid, st);
+        case ED_C64: return launch_tile_v<float2>(Q, qe2, B->nsub, grid, st);
+        case ED_F64: return launch_tile_v<double>(Q, qe2, B->nsub, grid, st);
+        case ED_C128: return launch_tile_v<double2>(Q, qe2, B->nsub, grid, st);
+      }
+      return ed_fail(ED_ERR_INVALID, "unknown dtype");
     }
   }
   P.x = x; P.y = y; P.r0 = r0; P.r1 = r1; P.partial = partial;

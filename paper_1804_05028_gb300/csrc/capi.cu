@@ -760,6 +760,8 @@ struct LanczosRun {
   bool cplx;
   cudaStream_t st;
   void *v[3];        // rotating: vprev, v, w (local or no reorthogonalisation)
+  void *ylo = nullptr;     // fp32 vectors: low words of the product (w is a double-float pair)
+  bool own_ylo = false;
   char *store = nullptr;   // full reorthogonalisation: slot k holds v_k
   int store_slots = 0;
   int reorth = ED_REORTH_LOCAL;
@@ -852,7 +854,7 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
     if (replay) { if ((rc = ed_launch_axpy(B, psi, v, (*coef)[j], L.dtype, L.st))) return rc; }
     if (replay && j == m_total - 1) break;
     ED_CK(cudaEventRecord(L.e0, L.st));
-    if ((rc = ed_launch_apply(B, L.J, L.Jz, v, w, L.dtype, 0, B->D, B->d_partial, L.st))) return rc;
+    if ((rc = ed_launch_apply(B, L.J, L.Jz, v, w, L.dtype, 0, B->D, B->d_partial, L.st, 0, L.ylo))) return rc;
     ED_CK(cudaEventRecord(L.e1, L.st));
     double a;
     if (replay) {
@@ -865,7 +867,7 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
     ED_CK(cudaEventElapsedTime(&ms, L.e0, L.e1));
     L.ms_apply += ms;
     const double bprev = j ? beta[j - 1] : 0.0;
-    if ((rc = ed_launch_axpy_norm(B, w, v, j ? vprev : nullptr, a, bprev, L.dtype, B->d_partial, nblk, L.st))) return rc;
+    if ((rc = ed_launch_axpy_norm(B, w, v, j ? vprev : nullptr, a, bprev, L.dtype, B->d_partial, nblk, L.st, L.ylo))) return rc;
     double b2 = 0, corr = 0;
     if (L.reorth != ED_REORTH_NONE) {
       if ((rc = reorth_step(L, j, w, v, j ? vprev : nullptr, !replay, &corr, &b2))) return rc;
@@ -951,6 +953,19 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
       return ed_fail(ED_ERR_OOM, "cannot allocate Lanczos vectors");
     }
   }
+  // fp32 vectors: the product's low words, so that the three-term update starts from y to
+  // about 48 bits (the fourth vector of the caller's workspace when it has one)
+  if (o.dtype == ED_F32 || o.dtype == ED_C64) {
+    if (!full && !own && o.work_bytes >= (int64_t)(4 * bytes)) {
+      L.ylo = (char *)o.work + 3 * bytes;
+    } else if (cudaMalloc(&L.ylo, bytes) == cudaSuccess) {
+      L.own_ylo = true;
+    } else {
+      cudaGetLastError();
+      if (own) for (int k = 0; k < 3; k++) cudaFree(L.v[k]);
+      return ed_fail(ED_ERR_OOM, "cannot allocate the low words of the product");
+    }
+  }
   // sweep scratch: partials of up to m_cap vectors per block, then their coefficients
   const int m_cap = full ? max_steps + 1 : 2;
   const int P = L.cplx ? 2 : 1;
@@ -959,6 +974,7 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
       cudaMalloc(&L.d_ro, sizeof(double) * (L.ro_coef_off + (size_t)m_cap * P)) != cudaSuccess) {
     cudaGetLastError();
     if (own) for (int k = 0; k < 3; k++) cudaFree(L.v[k]);
+    if (L.own_ylo) cudaFree(L.ylo);
     return ed_fail(ED_ERR_OOM, "cannot allocate the reorthogonalisation scratch");
   }
   ED_CK(cudaEventCreate(&L.e0));
@@ -1012,6 +1028,7 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
   }
   cudaStreamSynchronize(L.st);
   if (own) for (int k = 0; k < 3; k++) cudaFree(L.v[k]);
+  if (L.own_ylo) cudaFree(L.ylo);
   if (L.d_ro) cudaFree(L.d_ro);
   cudaEventDestroy(L.e0);
   cudaEventDestroy(L.e1);

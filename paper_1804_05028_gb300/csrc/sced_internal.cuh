@@ -335,9 +335,12 @@ int ed_cuda_fail(cudaError_t e, const char *what);
 int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target);
 // mode 0: y = H x (partial: optional <x, y> block partials); mode 1: per-class block partials
 // of Re <x | H_c x> (J, Jz: unit couplings) into partial[c * grid + block], y unused
+// ylo (fp32 / complex fp32 vectors only, may be null): receives the remainder of rounding
+// each y_i to fp32, so that y + ylo holds the product to about 48 bits; zeroed when the
+// kernel that runs cannot produce it
 int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const void *x, void *y,
                     int dtype, int64_t r0, int64_t r1, double *partial, cudaStream_t st,
-                    int mode = 0);
+                    int mode = 0, void *ylo = nullptr);
 int ed_launch_find_rep(const ed_basis *B, const uint64_t *states, int64_t n, uint64_t *rep,
                        int32_t *sym, int32_t *phase, int32_t *stab, int64_t *index,
                        cudaStream_t st);
@@ -345,15 +348,18 @@ int ed_launch_find_rep_two(const ed_basis *B, const uint64_t *states, int64_t n,
                            int32_t *phase, int32_t *stab, int64_t *index, cudaStream_t st);
 int ed_launch_dot(const ed_basis *B, const void *x, const void *y, int dtype, double *partial,
                   int nblk, cudaStream_t st);
+// w <- (w + wlo) - a v - b vprev, ||w||^2 partials; wlo (fp32 vectors, may be null) is the
+// low word of w from ed_launch_apply's ylo
 int ed_launch_axpy_norm(const ed_basis *B, void *w, const void *v, const void *vprev, double a,
-                        double b, int dtype, double *partial, int nblk, cudaStream_t st);
+                        double b, int dtype, double *partial, int nblk, cudaStream_t st,
+                        const void *wlo = nullptr);
 int ed_launch_scale(const ed_basis *B, void *v, double s, int dtype, cudaStream_t st);
 int ed_launch_axpy(const ed_basis *B, void *y, const void *x, double a, int dtype,
                    cudaStream_t st);
 int ed_launch_start(const ed_basis *B, void *v, uint64_t seed, int dtype, cudaStream_t st);
 int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, const void *x,
                          void *y, int dtype, int64_t r0, int64_t r1, double *partial,
-                         cudaStream_t st, int mode);
+                         cudaStream_t st, int mode, void *ylo = nullptr, bool *ylo_done = nullptr);
 int ed_build_full_table(const uint8_t *d_pbit, const uint8_t *d_flip, int N, int nsym,
                         uint64_t *out, cudaStream_t st);
 struct ed_batch;
