@@ -164,13 +164,17 @@ int ed_find_rep(const ed_basis *basis, const uint64_t *states, int64_t n, int32_
  * ed_apply_H -- y = H x on the symmetry-adapted basis, matrix-free (Sec. IV,
  * Eqs. 12-17 restated as a row-wise pull): for each row i, its diagonal, then for
  * each antiparallel bond the exchanged configuration, its representative by sublattice
- * coding (Alg. 2), its index through Limits and a binary search in the bucket, and
+ * coding (Alg. 2), its index through Limits (the bucket's first index plus the rank of
+ * the postfix in the bucket's bitmap, or a binary search in the bucket), and
  * y_i += (J/2) chi(h) sqrt(|Stab_j|/|Stab_i|) x_j.  No atomics; every y_i is written
- * once, with a fixed summation order (deterministic).
+ * once.  Deterministic: the same call gives the same bits.  The terms of 32
+ * consecutive rows are summed together, so a row range that starts elsewhere
+ * (ed_apply_H_rows, the chunks of ed_apply_H_host) may differ in the last bit.
  *   J, Jz: HOST arrays [n_classes].
  *   x, y: DEVICE arrays of dim elements of `dtype` (ED_F64 or ED_F32; the complex types
  *   for sectors with complex characters), caller-owned, must not overlap.
- *   dtype ED_F32 stores vectors in float and accumulates each row in float.
+ *   dtype ED_F32 stores vectors in float; each row is summed to about 48 bits
+ *   (double-float) and rounded once.
  *   Asynchronous on stream.  dim 0: no-op.
  * Errors: ED_ERR_INVALID (null pointers, dtype not matching the sector), ED_ERR_CUDA.
  */

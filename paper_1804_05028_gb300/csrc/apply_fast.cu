@@ -272,8 +272,12 @@ __device__ __forceinline__ Sm2 stage_two(const TwoParams &P, unsigned char *sm, 
 // Limits bucket, binary search of the postfixes in the bucket (Sec. IV); -1 when absent.
 // The fast path has N - r_bits <= 32, so the bucket key's raw bits and the postfix are
 // taken from the low 32 bits of the state.
+__device__ __forceinline__ int64_t lookup_ranked(const Sm2 &S, const TwoParams &P,
+                                                 uint32_t minrep, uint32_t low);
+
 __device__ __forceinline__ int64_t lookup_two(const Sm2 &S, const TwoParams &P, uint32_t minrep,
                                               uint32_t low) {
+  if (P.rlim) return lookup_ranked(S, P, minrep, low);
   const uint64_t r = ((uint64_t)minrep << P.L) | low;
   const uint32_t rk = S.top[(uint32_t)(r >> (P.N - P.r_bits))];
   if (rk == 0xFFFFu) return -1;
@@ -621,7 +625,7 @@ __device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, con
       defer = !find_rep_simple<NSUB, kE2>(S, P, s2, R);
     }
     if (!defer && !R.mixed) {
-      const int64_t j = P.rlim ? lookup_ranked(S, P, R.minrep, R.low) : lookup_two(S, P, R.minrep, R.low);
+      const int64_t j = lookup_two(S, P, R.minrep, R.low);
       if (j >= 0) {
         const V xj = gather_x(x, j);
         if constexpr (kF) {

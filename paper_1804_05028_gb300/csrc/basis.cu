@@ -551,5 +551,8 @@ int ed_build_device(ed_basis *B, cudaStream_t st, int bucket_target) {
   I.top_rank = B->d_top_rank;
   I.limits = B->d_limits;
   I.postfix = B->d_postfix;
+  I.rlim = reinterpret_cast<const uint4 *>(B->d_rlim);
+  I.rq_bits = B->rq_bits;
+  I.rpost_bits = B->rpost_bits;
   return ED_OK;
 }

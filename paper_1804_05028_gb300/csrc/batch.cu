@@ -84,6 +84,14 @@ constexpr int kBatchThreads = 256;
 __device__ __forceinline__ int64_t lookup_index32(const DevIndex &I, uint32_t s) {
   const uint32_t rk = __ldg(I.top_rank + (s >> (I.N - I.r_bits)));
   if (rk == ED_NO_RANK) return -1;
+  if (I.rlim) {   // ranked Limits: first index + rank of the postfix in the bucket's bitmap
+    const uint32_t key = (rk << I.rq_bits) | ((s >> I.rpost_bits) & ((1u << I.rq_bits) - 1u));
+    const uint4 rec = __ldg(I.rlim + key);
+    const uint32_t pf = s & ((1u << I.rpost_bits) - 1u);
+    const uint64_t bits = ((uint64_t)rec.w << 32) | rec.z;
+    if (!((bits >> pf) & 1ULL)) return -1;
+    return (int64_t)rec.x + __popcll(bits & ((1ULL << pf) - 1ULL));
+  }
   const uint32_t key = (rk << I.q_bits) | ((s >> I.post_bits) & ((1u << I.q_bits) - 1u));
   uint32_t lo = __ldg(I.limits + key), hi = __ldg(I.limits + key + 1);
   const uint32_t p = s & ((1u << I.post_bits) - 1u);

@@ -45,6 +45,8 @@ struct DevTables {
 //   key(s) = top_rank[s >> (N - r_bits)] << q_bits | (s >> post_bits) & (2^q - 1)
 //   limits[key] .. limits[key+1]: half-open range of Basis holding that key (Limits)
 //   postfix[i] = basis[i] & (2^post_bits - 1): what the in-bucket binary search compares
+//   rlim[key'] = {first index, 0, 64-bit bitmap of postfixes}: the ranked Limits over
+//   rq_bits raw bits and rpost_bits (<= 6) postfix bits, when built (else null)
 struct DevIndex {
   int N, r_bits, q_bits, post_bits;
   int post_bytes;  // 1, 2, 4 or 8
@@ -54,6 +56,8 @@ struct DevIndex {
   const uint32_t *top_rank;
   const uint32_t *limits;
   const void *postfix;
+  const uint4 *rlim;
+  int rq_bits, rpost_bits;
 };
 
 #define ED_NO_RANK 0xFFFFFFFFu
@@ -224,6 +228,15 @@ __device__ __forceinline__ int64_t lookup_index(const DevIndex &I, uint64_t s) {
   const uint32_t top = (uint32_t)(s >> (I.N - I.r_bits));
   const uint32_t rk = __ldg(I.top_rank + top);
   if (rk == ED_NO_RANK) return -1;
+  if (I.rlim) {   // ranked Limits: first index + rank of the postfix in the bucket's bitmap
+    const uint64_t key = ((uint64_t)rk << I.rq_bits) |
+                         ((s >> I.rpost_bits) & ((1ULL << I.rq_bits) - 1ULL));
+    const uint4 rec = __ldg(I.rlim + key);
+    const uint32_t pf = (uint32_t)(s & ((1ULL << I.rpost_bits) - 1ULL));
+    const uint64_t bits = ((uint64_t)rec.w << 32) | rec.z;
+    if (!((bits >> pf) & 1ULL)) return -1;
+    return (int64_t)rec.x + __popcll(bits & ((1ULL << pf) - 1ULL));
+  }
   const uint64_t qmask = (I.q_bits >= 64) ? ~0ULL : ((1ULL << I.q_bits) - 1ULL);
   const uint64_t key = ((uint64_t)rk << I.q_bits) | ((s >> I.post_bits) & qmask);
   const uint32_t lo = __ldg(I.limits + key), hi = __ldg(I.limits + key + 1);

@@ -68,11 +68,13 @@ def _check_sector(p, n_basis_samples, n_config_samples, n_rows):
     x = w.state_uniform(s, 1804)
     y = B.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
     # the host-buffer entry point runs the product in row chunks with the copies of y
-    # overlapped; rows are independent, so it must agree bit for bit
+    # overlapped; rows are independent, so it agrees with the single launch to rounding
+    # (the product groups 32 consecutive rows per warp and sums each row's terms in that
+    # group's order, so a chunk boundary inside a group may change the last bit)
     xp = torch.from_numpy(x).pin_memory()
     yp = torch.empty_like(xp).pin_memory()
     B.apply_H_host(xp, yp)
-    assert np.array_equal(yp.numpy(), y)
+    assert np.abs(yp.numpy() - y).max() <= 1e-14 * np.abs(y).max()
     rows = np.sort(rng.choice(D, n_rows, replace=False))
     y_ref = oracle.rows(p, s[rows], lambda q: w.state_uniform(q, 1804))
     scale = np.abs(y_ref).max()
