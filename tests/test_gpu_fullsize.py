@@ -9,11 +9,16 @@ sampled arbitrary configurations get the oracle's representative, stabiliser ord
 and a consistent index.  H x is compared row by row with the oracle's matrix-free
 rows on state-keyed input vectors.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 import workloads as w
+
+GOLDEN_SQ36 = os.path.join(os.path.dirname(__file__), "golden", "square36_e0.json")
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -150,4 +155,29 @@ def test_full_lattices_at_low_filling_every_row(p):
     xf32 = (lambda q: xf(q).astype(x32.dtype).astype(np.complex128 if cplx else np.float64))
     y_ref32 = oracle.rows(p, s, xf32)
     assert np.abs(y32 - y_ref32).max() <= 2e-6 * scale
+    B.close()
+
+
+def test_square36_e0_against_oracle():
+    """The 6x6 J1-J2 Gamma-A1 sector's ground-state energy against the oracle's
+    (tests/golden/square36_e0.json, written by tests/golden/make_square36_e0.py from
+    oracle/ alone: brute-force basis over all 2^36 configurations, the stored
+    symmetry-adapted matrix, fp64 Lanczos with full reorthogonalisation).
+
+    fp64: E0 within 1e-10 relative, and the first Lanczos coefficients from the same
+    state-keyed start vector within 1e-11 (alpha_0 = <v0|H|v0> sums the whole product);
+    mixed precision (fp32 vectors, fp64 scalars): E0 within the metric's 1e-9."""
+    import paper_1804_05028_gb300 as ed
+    g = json.load(open(GOLDEN_SQ36))
+    B = ed.build_basis_from(w.config_square36(0.5))
+    assert B.dim == g["dim"]
+    assert B.count_terms()[1] == g["offdiag_terms"]
+    r64 = B.lanczos(dtype=torch.float64, seed=1805)
+    assert r64["converged"]
+    assert abs(r64["E0"] - g["E0"]) <= 1e-10 * abs(g["E0"]), (r64["E0"], g["E0"])
+    na = min(5, len(g["alpha"]))
+    assert np.allclose(r64["alpha"][:na], g["alpha"][:na], rtol=0, atol=1e-11 * abs(g["E0"]))
+    assert np.allclose(r64["beta"][:na - 1], g["beta"][:na - 1], rtol=0, atol=1e-11 * abs(g["E0"]))
+    r32 = B.lanczos(dtype=torch.float32, seed=1805)
+    assert abs(r32["E0"] - g["E0"]) <= 1e-9 * abs(g["E0"]), (r32["E0"], g["E0"])
     B.close()
