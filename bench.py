@@ -48,6 +48,7 @@ WORKLOADS = {
 KERNEL_SOURCES = ["paper_1804_05028_gb300/csrc/apply.cu",
                   "paper_1804_05028_gb300/csrc/apply_fast.cu",
                   "paper_1804_05028_gb300/csrc/sced_internal.cuh",
+                  "paper_1804_05028_gb300/csrc/dfloat.cuh",
                   "paper_1804_05028_gb300/csrc/basis.cu",
                   "paper_1804_05028_gb300/csrc/capi.cu"]
 

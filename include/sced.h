@@ -296,7 +296,9 @@ int ed_count_terms(const ed_basis *basis, int64_t *n_flip, int64_t *n_offdiag, v
  * H = sum_c J_c H_c.  For a normalised ground state psi this is dE0/dJ_c (Hellmann-Feynman
  * theorem), the derivative the product's adjoint needs.  One pass of the product kernel
  * with per-class partial sums.
- *   Jz: HOST [n_classes].  x: DEVICE vector of dim elements, ED_F64 or ED_C128.
+ *   Jz: HOST [n_classes].  x: DEVICE vector of dim elements of dtype (the sector's real
+ *   or complex types; with fp32 vectors the terms are products of fp32 inputs, the class
+ *   sums are carried in double).
  *   out: HOST [n_classes].  Synchronous.  Errors: ED_ERR_INVALID, ED_ERR_CUDA.
  */
 int ed_expect_classes(ed_basis *basis, const double *Jz, const void *x, int32_t dtype,

@@ -25,7 +25,14 @@ class _GroundStateEnergy(torch.autograd.Function):
     def backward(ctx, grad):
         (J,) = ctx.saved_tensors
         B = ctx.basis
-        dt = torch.float64 if B.is_real else torch.complex128
+        # the ground state in the forward pass's precision: fp64 by default; with fp32
+        # vectors (the mixed form) psi is an fp32 vector and <psi|H_c|psi> is summed in
+        # double from fp32 products
+        mixed = ctx.kw.get("dtype") in (torch.float32, torch.complex64)
+        if mixed:
+            dt = torch.float32 if B.is_real else torch.complex64
+        else:
+            dt = torch.float64 if B.is_real else torch.complex128
         psi = torch.empty(B.dim, dtype=dt, device=f"cuda:{B.device}")
         kw = dict(ctx.kw)
         kw["dtype"] = dt
@@ -37,7 +44,11 @@ class _GroundStateEnergy(torch.autograd.Function):
 
 
 def ground_state_energy(basis, J, Jz=None, **lanczos_kw) -> torch.Tensor:
-    """E0 as a differentiable function of the per-class exchange J (CPU float64 tensor)."""
+    """E0 as a differentiable function of the per-class exchange J (CPU float64 tensor).
+
+    ``lanczos_kw`` goes to ``Basis.lanczos``; ``dtype=torch.float32`` (or complex64) runs
+    both passes in the mixed form, whose gradient carries the fp32 ground state's error
+    (first order in it, about 1e-7 relative) instead of fp64's."""
     if not isinstance(J, torch.Tensor):
         J = torch.tensor(J, dtype=torch.float64)
     return _GroundStateEnergy.apply(J, basis, Jz, lanczos_kw)

@@ -265,12 +265,14 @@ __global__ void dot_kernel(const V *x, const V *y, int64_t n, double *partial) {
 }
 
 // w <- w - a v - b vprev ; partial ||w||^2   (vprev may be null).  fp64 vectors in fp64;
-// fp32 vectors in double-float (a and b split into two fp32 words each, exact products),
-// rounded once, with the norm's per-thread sum in double-float as well: the fp64 pipe of
-// this GPU is too slow for a pass over the whole vector.
+// fp32 vectors in double-float (a and b split into two fp32 words each, exact products):
+// with wlo (may be null) w enters as the pair (w, wlo) -- the product's value and its
+// rounding remainder -- and leaves the same way, so that the update rounds nothing; the
+// norm is that of the pair.  The fp64 pipe of this GPU is too slow for a pass of fp64
+// arithmetic over the whole vector.
 template <typename V>
 __global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, double b,
-                                 int64_t n, double *partial, const V *wlo) {
+                                 int64_t n, double *partial, V *wlo) {
   using A = typename Vt<V>::A;
   constexpr bool kF = sizeof(A) == 4;
   double acc = 0;
@@ -293,17 +295,22 @@ __global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, dou
         df_sub_scaled(rh, rl, bh, bl, p0.x);
         df_sub_scaled(ih, il, bh, bl, p0.y);
       }
-      V o; o.x = df_round(rh, rl); o.y = df_round(ih, il);
+      V o, r;
+      df_store(rh, rl, o.x, r.x);
+      df_store(ih, il, o.y, r.y);
       w[i] = o;
-      df_add_prod(nh, nl, o.x, o.x);
-      df_add_prod(nh, nl, o.y, o.y);
+      if (wlo) wlo[i] = r; else { r.x = 0.f; r.y = 0.f; }
+      df_add_sq(nh, nl, o.x, r.x);
+      df_add_sq(nh, nl, o.y, r.y);
     } else if constexpr (kF) {
       float hi = w[i], lo = wlo ? wlo[i] : 0.f;
       df_sub_scaled(hi, lo, ah, al, v[i]);
       if (vprev) df_sub_scaled(hi, lo, bh, bl, vprev[i]);
-      const float o = df_round(hi, lo);
+      float o, r;
+      df_store(hi, lo, o, r);
       w[i] = o;
-      df_add_prod(nh, nl, o, o);
+      if (wlo) wlo[i] = r; else r = 0.f;
+      df_add_sq(nh, nl, o, r);
     } else if constexpr (Vt<V>::cplx) {
       double wr = (double)w[i].x - a * (double)v[i].x;
       double wi = (double)w[i].y - a * (double)v[i].y;
@@ -323,11 +330,36 @@ __global__ void axpy_norm_kernel(V *w, const V *v, const V *vprev, double a, dou
   block_reduce_store<double>(acc, partial, blockIdx.x);
 }
 
+// v <- s v; with vlo (fp32 vectors, may be null) v enters as the pair (v, vlo) and the
+// product is rounded once
 template <typename V>
-__global__ void scale_kernel(V *v, double s, int64_t n) {
+__global__ void scale_kernel(V *v, double s, int64_t n, const V *vlo) {
   using A = typename Vt<V>::A;
+  constexpr bool kF = sizeof(A) == 4;
+  float sh = 0.f, sl = 0.f;
+  if constexpr (kF) df_split(s, sh, sl);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (kF) {
+      if (vlo) {
+        if constexpr (Vt<V>::cplx) {
+          const V a = v[i], l = vlo[i];
+          float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+          df_sub_scaled(rh, rl, -sh, -sl, a.x);
+          df_sub_scaled(rh, rl, -sh, -sl, l.x);
+          df_sub_scaled(ih, il, -sh, -sl, a.y);
+          df_sub_scaled(ih, il, -sh, -sl, l.y);
+          V o; o.x = df_round(rh, rl); o.y = df_round(ih, il);
+          v[i] = o;
+        } else {
+          float hi = 0.f, lo = 0.f;
+          df_sub_scaled(hi, lo, -sh, -sl, v[i]);
+          df_sub_scaled(hi, lo, -sh, -sl, vlo[i]);
+          v[i] = df_round(hi, lo);
+        }
+        continue;
+      }
+    }
     if constexpr (Vt<V>::cplx) { V o = v[i]; o.x = (A)(o.x * s); o.y = (A)(o.y * s); v[i] = o; }
     else v[i] = (A)((double)v[i] * s);
   }
@@ -380,7 +412,7 @@ int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const 
                     void *y, int dtype, int64_t r0, int64_t r1, double *partial,
                     cudaStream_t st, int mode, void *ylo) {
   if (r1 <= r0) return ED_OK;
-  if (!getenv("SCED_GENERIC_APPLY")) {
+  {  // the specialised two-level kernels first; the generic kernel serves what they cannot
     bool done = false;
     const int rc = ed_launch_apply_fast(B, J, Jz, x, y, dtype, r0, r1, partial, st, mode, ylo, &done);
     if (rc != ED_ERR_UNSUPPORTED) {
@@ -444,9 +476,13 @@ int ed_launch_apply(const ed_basis *B, const double *J, const double *Jz, const 
   const bool sg = P.stage_tables != 0;
   if (mode == 1) {
     if (!partial || B->n_classes * grid > B->n_partial) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
-    if (dtype == ED_F64) return sg ? launch_apply_t<double, true, 1>(P, grid, st) : launch_apply_t<double, false, 1>(P, grid, st);
-    if (dtype == ED_C128) return sg ? launch_apply_t<double2, true, 1>(P, grid, st) : launch_apply_t<double2, false, 1>(P, grid, st);
-    return ed_fail(ED_ERR_INVALID, "class expectations need fp64 vectors");
+    switch (dtype) {
+      case ED_F64: return sg ? launch_apply_t<double, true, 1>(P, grid, st) : launch_apply_t<double, false, 1>(P, grid, st);
+      case ED_F32: return sg ? launch_apply_t<float, true, 1>(P, grid, st) : launch_apply_t<float, false, 1>(P, grid, st);
+      case ED_C128: return sg ? launch_apply_t<double2, true, 1>(P, grid, st) : launch_apply_t<double2, false, 1>(P, grid, st);
+      case ED_C64: return sg ? launch_apply_t<float2, true, 1>(P, grid, st) : launch_apply_t<float2, false, 1>(P, grid, st);
+    }
+    return ed_fail(ED_ERR_INVALID, "unknown dtype");
   }
   switch (dtype) {
     case ED_F64: return sg ? launch_apply_t<double, true>(P, grid, st) : launch_apply_t<double, false>(P, grid, st);
@@ -495,17 +531,18 @@ int ed_launch_dot(const ed_basis *B, const void *x, const void *y, int dtype, do
 
 int ed_launch_axpy_norm(const ed_basis *B, void *w, const void *v, const void *vprev, double a,
                         double b, int dtype, double *partial, int nblk, cudaStream_t st,
-                        const void *wlo) {
+                        void *wlo) {
   ED_DISPATCH(dtype, (axpy_norm_kernel<V><<<nblk, 256, 0, st>>>((V *)w, (const V *)v,
                                                                 (const V *)vprev, a, b, B->D,
-                                                                partial, (const V *)wlo)));
+                                                                partial, (V *)wlo)));
   ED_CK(cudaGetLastError());
   return ED_OK;
 }
 
-int ed_launch_scale(const ed_basis *B, void *v, double s, int dtype, cudaStream_t st) {
+int ed_launch_scale(const ed_basis *B, void *v, double s, int dtype, cudaStream_t st,
+                    const void *vlo) {
   const int grid = grid_for(B, B->D, 8);
-  ED_DISPATCH(dtype, (scale_kernel<V><<<grid, 256, 0, st>>>((V *)v, s, B->D)));
+  ED_DISPATCH(dtype, (scale_kernel<V><<<grid, 256, 0, st>>>((V *)v, s, B->D, (const V *)vlo)));
   ED_CK(cudaGetLastError());
   return ED_OK;
 }

@@ -1030,7 +1030,7 @@ int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, c
   if (rc) return rc;
   // the product: the term-parallel kernel (level-2 tables staged when they fit with the
   // per-warp term lists, else read from global memory)
-  if (mode == 0 && !getenv("SCED_ROW_KERNEL")) {
+  if (mode == 0) {
     TwoParams Q;
     bool qe2 = e2;
     int qrc = make_params(B, J, Jz, qe2, Q, (qe2 ? kTileThreadsE2 : kTileThreads) / 32);
@@ -1068,9 +1068,13 @@ int ed_launch_apply_fast(const ed_basis *B, const double *J, const double *Jz, c
   B->last_apply_grid = grid;
   if (mode == 1) {
     if (!partial || B->n_classes * grid > B->n_partial) return ed_fail(ED_ERR_INVALID, "partial buffer too small");
-    if (dtype == ED_F64) return launch_v<double, 1>(P, e2, B->nsub, grid, st);
-    if (dtype == ED_C128) return launch_v<double2, 1>(P, e2, B->nsub, grid, st);
-    return ed_fail(ED_ERR_INVALID, "class expectations need fp64 vectors");
+    switch (dtype) {
+      case ED_F64: return launch_v<double, 1>(P, e2, B->nsub, grid, st);
+      case ED_F32: return launch_v<float, 1>(P, e2, B->nsub, grid, st);
+      case ED_C128: return launch_v<double2, 1>(P, e2, B->nsub, grid, st);
+      case ED_C64: return launch_v<float2, 1>(P, e2, B->nsub, grid, st);
+    }
+    return ed_fail(ED_ERR_INVALID, "unknown dtype");
   }
   switch (dtype) {
     case ED_F64: return launch_v<double>(P, e2, B->nsub, grid, st);

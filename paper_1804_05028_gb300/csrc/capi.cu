@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <unordered_map>
@@ -727,7 +728,6 @@ extern "C" int ed_count_terms(const ed_basis *B, int64_t *n_flip, int64_t *n_off
 extern "C" int ed_expect_classes(ed_basis *B, const double *Jz, const void *x, int32_t dtype,
                                  double *out, void *stream) {
   if (!B || !Jz || !out) return ed_fail(ED_ERR_INVALID, "null argument");
-  if (dtype != ED_F64 && dtype != ED_C128) return ed_fail(ED_ERR_INVALID, "needs fp64 vectors");
   int rc = check_dtype(B, dtype);
   if (rc) return rc;
   for (int c = 0; c < B->n_classes; c++) out[c] = 0.0;
@@ -793,10 +793,10 @@ int reorth_step(LanczosRun &L, int j, void *w, const void *v, const void *vprev,
   for (int sw = 0; sw < sweeps; sw++) {
     int rc, jj;
     if (L.reorth == ED_REORTH_FULL) {
-      rc = ed_launch_reorth_sweep(B, w, L.store, nullptr, nullptr, j + 1, L.dtype, L.d_ro, c, L.st);
+      rc = ed_launch_reorth_sweep(B, w, L.store, nullptr, nullptr, j + 1, L.dtype, L.d_ro, c, L.st, L.ylo);
       jj = j;
     } else {
-      rc = ed_launch_reorth_sweep(B, w, nullptr, v, vprev, j ? 2 : 1, L.dtype, L.d_ro, c, L.st);
+      rc = ed_launch_reorth_sweep(B, w, nullptr, v, vprev, j ? 2 : 1, L.dtype, L.d_ro, c, L.st, L.ylo);
       jj = 0;
     }
     if (rc) return rc;
@@ -902,7 +902,7 @@ int lanczos_pass(LanczosRun &L, const ed_lanczos_opts *o, int max_steps, bool fi
       if (stop || j + 1 == max_steps) break;
       beta.push_back(b);
     }
-    if ((rc = ed_launch_scale(B, w, 1.0 / b, L.dtype, L.st))) return rc;
+    if ((rc = ed_launch_scale(B, w, 1.0 / b, L.dtype, L.st, L.ylo))) return rc;
     if (!full) { void *t = vprev; vprev = v; v = w; w = t; }
   }
   return ED_OK;

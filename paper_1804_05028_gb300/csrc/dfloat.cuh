@@ -44,3 +44,15 @@ __device__ __forceinline__ double df_value(float hi, float lo) { return (double)
 
 // the fp32 word nearest to hi + lo
 __device__ __forceinline__ float df_round(float hi, float lo) { return __fadd_rn(hi, lo); }
+
+// the pair (hi, lo) as the fp32 word o nearest to it plus the fp32 word r nearest to the
+// rest, and the square of o + r added to (nh, nl)
+__device__ __forceinline__ void df_store(float hi, float lo, float &o, float &r) {
+  o = __fadd_rn(hi, lo);
+  r = __fadd_rn(__fsub_rn(hi, o), lo);
+}
+
+__device__ __forceinline__ void df_add_sq(float &nh, float &nl, float o, float r) {
+  df_add_prod(nh, nl, o, o);
+  df_add_prod(nh, nl, __fadd_rn(o, o), r);
+}

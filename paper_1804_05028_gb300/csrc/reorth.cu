@@ -61,8 +61,8 @@ __device__ __forceinline__ double warp_sum(double d) {
 // block's warps in order) into partial[(k * P + part) * nblk + blk], P = 2 for complex
 // (re, im) else 1.
 template <typename V>
-__global__ void __launch_bounds__(kThreads) multidot_kernel(VecSet S, const V *w, int64_t n,
-                                                            double *partial) {
+__global__ void __launch_bounds__(kThreads) multidot_kernel(VecSet S, const V *w, const V *wlo,
+                                                            int64_t n, double *partial) {
   using A = typename Rv<V>::A;
   constexpr bool kC = Rv<V>::cplx;
   constexpr bool kF = std::is_same<A, float>::value;
@@ -77,17 +77,25 @@ __global__ void __launch_bounds__(kThreads) multidot_kernel(VecSet S, const V *w
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
     const V wv = w[i];
+    V wl;
+    if constexpr (kF) {
+      if constexpr (kC) { wl.x = 0.f; wl.y = 0.f; } else { wl = 0.f; }
+      if (wlo) wl = wlo[i];
+    }
 #pragma unroll
     for (int q = 0; q < kGroup; q++) {
       if (q < kn) {
         const V a = vec<V>(S, k0 + q)[i];
-        if constexpr (kF && kC) {          // conj(a) * w
+        if constexpr (kF && kC) {          // conj(a) * (w + wlo)
           df_add_prod(rh[q], rl[q], a.x, wv.x);
           df_add_prod(rh[q], rl[q], a.y, wv.y);
           df_add_prod(ih[q], il[q], a.x, wv.y);
           df_add_prod(ih[q], il[q], -a.y, wv.x);
+          rl[q] = __fmaf_rn(a.x, wl.x, __fmaf_rn(a.y, wl.y, rl[q]));
+          il[q] = __fmaf_rn(a.x, wl.y, __fmaf_rn(-a.y, wl.x, il[q]));
         } else if constexpr (kF) {
           df_add_prod(rh[q], rl[q], a, wv);
+          rl[q] = __fmaf_rn(a, wl, rl[q]);
         } else if constexpr (kC) {
           re[q] += a.x * wv.x + a.y * wv.y;
           im[q] += a.x * wv.y - a.y * wv.x;
@@ -152,7 +160,7 @@ __device__ __forceinline__ void block_sum_store(double d, double *out, int slot)
 // vectors: fp64.
 template <typename V>
 __global__ void __launch_bounds__(kThreads) update_kernel(VecSet S, const double *c, V *w,
-                                                          int64_t n, double *partial) {
+                                                          V *wlo, int64_t n, double *partial) {
   using A = typename Rv<V>::A;
   constexpr bool kC = Rv<V>::cplx;
   constexpr bool kF = std::is_same<A, float>::value;
@@ -171,6 +179,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(VecSet S, const double
     if constexpr (kF && kC) {
       const V w0 = w[i];
       float rh = w0.x, rl = 0.f, ih = w0.y, il = 0.f;
+      if (wlo) { const V l0 = wlo[i]; rl = l0.x; il = l0.y; }
 #pragma unroll 4
       for (int k = 0; k < S.m; k++) {
         const V a = vec<V>(S, k)[i];
@@ -180,19 +189,22 @@ __global__ void __launch_bounds__(kThreads) update_kernel(VecSet S, const double
         df_sub_scaled(ih, il, crh, crl, a.y);     // - cr a.y
         df_sub_scaled(ih, il, cih, cil, a.x);     // - ci a.x
       }
-      V o;
-      o.x = df_round(rh, rl);
-      o.y = df_round(ih, il);
+      V o, r;
+      df_store(rh, rl, o.x, r.x);
+      df_store(ih, il, o.y, r.y);
       w[i] = o;
-      df_add_prod(nh, nl, o.x, o.x);
-      df_add_prod(nh, nl, o.y, o.y);
+      if (wlo) wlo[i] = r; else { r.x = 0.f; r.y = 0.f; }
+      df_add_sq(nh, nl, o.x, r.x);
+      df_add_sq(nh, nl, o.y, r.y);
     } else if constexpr (kF) {
-      float hi = w[i], lo = 0.f;
+      float hi = w[i], lo = wlo ? wlo[i] : 0.f;
 #pragma unroll 4
       for (int k = 0; k < S.m; k++) df_sub_scaled(hi, lo, cf[2 * k], cf[2 * k + 1], vec<V>(S, k)[i]);
-      const float o = df_round(hi, lo);
+      float o, r;
+      df_store(hi, lo, o, r);
       w[i] = o;
-      df_add_prod(nh, nl, o, o);
+      if (wlo) wlo[i] = r; else r = 0.f;
+      df_add_sq(nh, nl, o, r);
     } else if constexpr (kC) {
       double wr = w[i].x, wi = w[i].y;
 #pragma unroll 4
@@ -297,7 +309,7 @@ int ed_reorth_grid(const ed_basis *B) { return 4 * B->sm_count; }
 // partials in partial[0 .. grid).  partial must hold m * P * grid doubles.
 int ed_launch_reorth_sweep(const ed_basis *B, void *w, const void *base, const void *p0,
                            const void *p1, int m, int dtype, double *partial, double *c,
-                           cudaStream_t st) {
+                           cudaStream_t st, void *wlo) {
   if (m <= 0) return ED_OK;
   const bool cplx = dtype == ED_C128 || dtype == ED_C64;
   const int P = cplx ? 2 : 1;
@@ -307,11 +319,11 @@ int ed_launch_reorth_sweep(const ed_basis *B, void *w, const void *base, const v
   if (smem_upd > 48 * 1024) return ed_fail(ED_ERR_UNSUPPORTED, "too many vectors in one sweep");
   const dim3 dgrid(grid, (m + kGroup - 1) / kGroup);
   RO_DISPATCH(dtype, {
-    multidot_kernel<V><<<dgrid, kThreads, 0, st>>>(S, (const V *)w, B->D, partial);
+    multidot_kernel<V><<<dgrid, kThreads, 0, st>>>(S, (const V *)w, (const V *)wlo, B->D, partial);
     ED_CK(cudaGetLastError());
     coef_kernel<<<m * P, kThreads, 0, st>>>(partial, grid, c);
     ED_CK(cudaGetLastError());
-    update_kernel<V><<<grid, kThreads, smem_upd, st>>>(S, c, (V *)w, B->D, partial);
+    update_kernel<V><<<grid, kThreads, smem_upd, st>>>(S, c, (V *)w, (V *)wlo, B->D, partial);
     ED_CK(cudaGetLastError());
   });
   return ED_OK;

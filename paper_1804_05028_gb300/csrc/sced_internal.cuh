@@ -361,12 +361,15 @@ int ed_launch_find_rep_two(const ed_basis *B, const uint64_t *states, int64_t n,
                            int32_t *phase, int32_t *stab, int64_t *index, cudaStream_t st);
 int ed_launch_dot(const ed_basis *B, const void *x, const void *y, int dtype, double *partial,
                   int nblk, cudaStream_t st);
-// w <- (w + wlo) - a v - b vprev, ||w||^2 partials; wlo (fp32 vectors, may be null) is the
-// low word of w from ed_launch_apply's ylo
+// (w, wlo) <- (w + wlo) - a v - b vprev, ||w + wlo||^2 partials; wlo (fp32 vectors, may
+// be null) holds the low words of w: on entry those of the product (ed_launch_apply's
+// ylo), on exit those of the update
 int ed_launch_axpy_norm(const ed_basis *B, void *w, const void *v, const void *vprev, double a,
                         double b, int dtype, double *partial, int nblk, cudaStream_t st,
-                        const void *wlo = nullptr);
-int ed_launch_scale(const ed_basis *B, void *v, double s, int dtype, cudaStream_t st);
+                        void *wlo = nullptr);
+// v <- s (v + vlo), rounded once (vlo: fp32 vectors, may be null)
+int ed_launch_scale(const ed_basis *B, void *v, double s, int dtype, cudaStream_t st,
+                    const void *vlo = nullptr);
 int ed_launch_axpy(const ed_basis *B, void *y, const void *x, double a, int dtype,
                    cudaStream_t st);
 int ed_launch_start(const ed_basis *B, void *v, uint64_t seed, int dtype, cudaStream_t st);
@@ -384,6 +387,6 @@ int ed_launch_copy(const ed_basis *B, void *dst, const void *src, int dtype, cud
 int ed_reorth_grid(const ed_basis *B);
 int ed_launch_reorth_sweep(const ed_basis *B, void *w, const void *base, const void *p0,
                            const void *p1, int m, int dtype, double *partial, double *c,
-                           cudaStream_t st);
+                           cudaStream_t st, void *wlo = nullptr);
 int ed_launch_combine(const ed_basis *B, void *psi, const void *base, int m, const double *s,
                       int dtype, cudaStream_t st);

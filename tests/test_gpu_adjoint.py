@@ -76,6 +76,52 @@ def test_dE0_dJ_autograd_fd_and_hellmann_feynman(J2):
     assert abs(E.item() - ev[0]) < 1e-10 * abs(ev[0])
 
 
+@pytest.mark.parametrize("p", [
+    w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=0.5, n_sublat=4, n_up=8),
+    w.square_torus(4, momentum=(1, 0), point_irrep=1, J2=0.5, n_sublat=2, n_up=8),
+], ids=lambda p: p.name)
+def test_class_expectations_fp32(p):
+    """The class-resolved pass on fp32 vectors (the mixed form's adjoint): every class
+    against the oracle in fp64 on the same fp32-representable vector.  Each term is a
+    product of an fp32 input and an fp32 weight, summed in fp32 per row and class and in
+    double across rows.  Recursive fp32 summation of a row's at most 32 terms (one per
+    bond), after the rounding of the weight and of each product, is off by at most
+    (32 + 3) u sum |terms| (u = 2^-24): the bound is 40 u x^T |H_c| x."""
+    B = _ed().build_basis_from(p)
+    s, _ = B.export()
+    x = w.state_uniform(s, 1806)
+    x = (x / np.linalg.norm(x)).astype(np.float32 if B.is_real else np.complex64)
+    got = B.expect_classes(torch.from_numpy(x).cuda(), Jz=p.Jz)
+    xd = x.astype(np.float64 if B.is_real else np.complex128)
+    for c in range(p.n_classes):
+        Hc, _, _ = oracle.hamiltonian(_unit(p, c, p.Jz))
+        ref = np.vdot(xd, Hc @ xd).real
+        bound = 40 * 2.0 ** -24 * np.abs(xd).conj() @ (abs(Hc) @ np.abs(xd))
+        assert abs(got[c] - ref) <= bound, (c, got[c], ref, bound)
+
+
+def test_dE0_dJ_mixed_against_oracle():
+    """autograd in the mixed form (fp32 vectors both passes) on the 4x4 J1-J2 sector:
+    the gradient against the oracle's dense Hellmann-Feynman value.  The fp32 ground
+    state's error enters the gradient to first order: with fp32 storage its residual
+    stops near u ||H|| (u = 2^-24), and the gradient error is at most about
+    2 ||H_c|| ||residual|| / gap, about 1e-5 here; the test asks 2e-5 and Euler's identity
+    sum_c J_c g_c = E0 to the same bound."""
+    from paper_1804_05028_gb300.autograd import ground_state_energy
+    p = w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=0.5, n_sublat=4, n_up=8)
+    B = _ed().build_basis_from(p)
+    J = torch.tensor([1.0, 0.5], dtype=torch.float64, requires_grad=True)
+    E = ground_state_energy(B, J, dtype=torch.float32)
+    E.backward()
+    g = J.grad.numpy()
+    H, bs, _ = oracle.hamiltonian(p)
+    ev, vec = np.linalg.eigh(H.toarray())
+    psi = vec[:, 0]
+    hf = np.array([psi @ (oracle.hamiltonian(_unit(p, c))[0] @ psi) for c in range(2)])
+    assert np.all(np.abs(g - hf) <= 2e-5), (g, hf)
+    assert abs(1.0 * g[0] + 0.5 * g[1] - ev[0]) <= 2e-5, (g, ev[0])
+
+
 @pytest.fixture(scope="module")
 def square36():
     B = _ed().build_basis_from(w.config_square36(0.5))
@@ -112,3 +158,16 @@ def test_dE0_dJ_square36_scan(square36, J2):
     fd_j1 = (e(1.0 + h, J2) - e(1.0 - h, J2)) / (2 * h)
     assert abs(g[0] - fd_j1) < 2e-6, (g[0], fd_j1)
     assert abs(1.0 * g[0] + J2 * g[1] - E.item()) < 1e-8 * abs(E.item())
+
+
+def test_dE0_dJ_square36_mixed(square36):
+    """The mixed-form gradient on the full 6x6 sector at J2 = 0.5 against the fp64 one
+    (bound as in test_dE0_dJ_mixed_against_oracle, relative to |E0|)."""
+    from paper_1804_05028_gb300.autograd import ground_state_energy
+    g = []
+    for dt in (torch.float64, torch.float32):
+        J = torch.tensor([1.0, 0.5], dtype=torch.float64, requires_grad=True)
+        E = ground_state_energy(square36, J, dtype=dt)
+        E.backward()
+        g.append(J.grad.numpy().copy())
+    assert np.all(np.abs(g[1] - g[0]) <= 2e-5 * 18.2), g
