@@ -54,6 +54,45 @@ __device__ __forceinline__ double warp_sum(double d) {
   return d;
 }
 
+// Rows per thread and iteration: the loads of U rows (U grid-stride apart, so every load
+// stays coalesced) are issued together, which keeps enough bytes in flight to stream
+// from HBM; a thread still visits its rows in increasing order, so the sums do not
+// depend on U.
+template <typename V> struct RowsPer { static constexpr int U = 1; };
+template <> struct RowsPer<float> { static constexpr int U = 4; };
+template <> struct RowsPer<double> { static constexpr int U = 2; };
+template <> struct RowsPer<float2> { static constexpr int U = 2; };
+
+// conj(a) (w + wl) into one accumulator (double-float for fp32 vectors)
+template <typename V>
+__device__ __forceinline__ void md_acc(double &re, double &im, float &rh, float &rl, float &ih,
+                                       float &il, const V a, const V wv, const V wl) {
+  using A = typename Rv<V>::A;
+  constexpr bool kC = Rv<V>::cplx;
+  constexpr bool kF = std::is_same<A, float>::value;
+  if constexpr (kF && kC) {
+    df_add_prod(rh, rl, a.x, wv.x);
+    df_add_prod(rh, rl, a.y, wv.y);
+    df_add_prod(ih, il, a.x, wv.y);
+    df_add_prod(ih, il, -a.y, wv.x);
+    rl = __fmaf_rn(a.x, wl.x, __fmaf_rn(a.y, wl.y, rl));
+    il = __fmaf_rn(a.x, wl.y, __fmaf_rn(-a.y, wl.x, il));
+  } else if constexpr (kF) {
+    df_add_prod(rh, rl, a, wv);
+    rl = __fmaf_rn(a, wl, rl);
+  } else if constexpr (kC) {
+    re += a.x * wv.x + a.y * wv.y;
+    im += a.x * wv.y - a.y * wv.x;
+  } else {
+    re += a * wv;
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ V zero_v() {
+  if constexpr (Rv<V>::cplx) { V z; z.x = 0; z.y = 0; return z; } else { return V(0); }
+}
+
 // Every thread keeps accumulators for a group of kGroup vectors (blockIdx.y selects the
 // group) over its grid-stride rows: w[i] is read once per group and the kGroup loads of
 // u_k[i] are independent.  fp32 vectors accumulate exact products in double-float, fp64
@@ -61,12 +100,13 @@ __device__ __forceinline__ double warp_sum(double d) {
 // block's warps in order) into partial[(k * P + part) * nblk + blk], P = 2 for complex
 // (re, im) else 1.
 template <typename V>
-__global__ void __launch_bounds__(kThreads) multidot_kernel(VecSet S, const V *w, const V *wlo,
+__global__ void __launch_bounds__(kThreads, 4) multidot_kernel(VecSet S, const V *w, const V *wlo,
                                                             int64_t n, double *partial) {
   using A = typename Rv<V>::A;
   constexpr bool kC = Rv<V>::cplx;
   constexpr bool kF = std::is_same<A, float>::value;
   constexpr int P = kC ? 2 : 1;
+  constexpr int U = RowsPer<V>::U;
   __shared__ double red[kGroup * P][kWarps];
   const int k0 = blockIdx.y * kGroup;
   const int kn = min(kGroup, S.m - k0);
@@ -74,36 +114,33 @@ __global__ void __launch_bounds__(kThreads) multidot_kernel(VecSet S, const V *w
   float rh[kGroup], rl[kGroup], ih[kGroup], il[kGroup];   // fp32 vectors: double-float
 #pragma unroll
   for (int q = 0; q < kGroup; q++) { re[q] = im[q] = 0.0; rh[q] = rl[q] = ih[q] = il[q] = 0.f; }
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kThreads) {
-    const V wv = w[i];
-    V wl;
-    if constexpr (kF) {
-      if constexpr (kC) { wl.x = 0.f; wl.y = 0.f; } else { wl = 0.f; }
-      if (wlo) wl = wlo[i];
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  for (; i + (U - 1) * stride < n; i += U * stride) {
+    V wv[U], wl[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      wv[u] = w[i + u * stride];
+      wl[u] = (kF && wlo) ? wlo[i + u * stride] : zero_v<V>();
     }
 #pragma unroll
     for (int q = 0; q < kGroup; q++) {
       if (q < kn) {
-        const V a = vec<V>(S, k0 + q)[i];
-        if constexpr (kF && kC) {          // conj(a) * (w + wlo)
-          df_add_prod(rh[q], rl[q], a.x, wv.x);
-          df_add_prod(rh[q], rl[q], a.y, wv.y);
-          df_add_prod(ih[q], il[q], a.x, wv.y);
-          df_add_prod(ih[q], il[q], -a.y, wv.x);
-          rl[q] = __fmaf_rn(a.x, wl.x, __fmaf_rn(a.y, wl.y, rl[q]));
-          il[q] = __fmaf_rn(a.x, wl.y, __fmaf_rn(-a.y, wl.x, il[q]));
-        } else if constexpr (kF) {
-          df_add_prod(rh[q], rl[q], a, wv);
-          rl[q] = __fmaf_rn(a, wl, rl[q]);
-        } else if constexpr (kC) {
-          re[q] += a.x * wv.x + a.y * wv.y;
-          im[q] += a.x * wv.y - a.y * wv.x;
-        } else {
-          re[q] += a * wv;
-        }
+        const V *uk = vec<V>(S, k0 + q);
+        V a[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) a[u] = uk[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < U; u++) md_acc<V>(re[q], im[q], rh[q], rl[q], ih[q], il[q], a[u], wv[u], wl[u]);
       }
     }
+  }
+  for (; i < n; i += stride) {
+    const V wv = w[i];
+    const V wl = (kF && wlo) ? wlo[i] : zero_v<V>();
+#pragma unroll
+    for (int q = 0; q < kGroup; q++)
+      if (q < kn) md_acc<V>(re[q], im[q], rh[q], rl[q], ih[q], il[q], vec<V>(S, k0 + q)[i], wv, wl);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -158,13 +195,96 @@ __device__ __forceinline__ void block_sum_store(double d, double *out, int slot)
 // w <- w - sum_k c_k u_k, rounded once; partial[blk] = the block's ||w||^2.  fp32 vectors:
 // every coefficient split into two fp32 words and the sum carried in double-float; fp64
 // vectors: fp64.
+// The running value of one row of w during the update: double-float words for fp32
+// vectors (real and imaginary parts), fp64 otherwise.
+template <typename V> struct Row;
+template <> struct Row<float> { float h, l; };
+template <> struct Row<float2> { float rh, rl, ih, il; };
+template <> struct Row<double> { double t; };
+template <> struct Row<double2> { double r, i; };
+
 template <typename V>
-__global__ void __launch_bounds__(kThreads) update_kernel(VecSet S, const double *c, V *w,
+__device__ __forceinline__ Row<V> row_load(const V *w, const V *wlo, int64_t i) {
+  Row<V> R;
+  if constexpr (std::is_same<V, float>::value) {
+    R.h = w[i];
+    R.l = wlo ? wlo[i] : 0.f;
+  } else if constexpr (std::is_same<V, float2>::value) {
+    const V w0 = w[i];
+    R.rh = w0.x; R.ih = w0.y; R.rl = 0.f; R.il = 0.f;
+    if (wlo) { const V l0 = wlo[i]; R.rl = l0.x; R.il = l0.y; }
+  } else if constexpr (std::is_same<V, double>::value) {
+    R.t = w[i];
+  } else {
+    const V w0 = w[i];
+    R.r = w0.x; R.i = w0.y;
+  }
+  return R;
+}
+
+// R -= c_k a (cs: fp64 coefficients [m][P]; cf: the same as two fp32 words each)
+template <typename V>
+__device__ __forceinline__ void row_sub(Row<V> &R, const double *cs, const float *cf, int k, const V a) {
+  if constexpr (std::is_same<V, float>::value) {
+    df_sub_scaled(R.h, R.l, cf[2 * k], cf[2 * k + 1], a);
+  } else if constexpr (std::is_same<V, float2>::value) {
+    const float crh = cf[4 * k], crl = cf[4 * k + 1], cih = cf[4 * k + 2], cil = cf[4 * k + 3];
+    df_sub_scaled(R.rh, R.rl, crh, crl, a.x);     // - cr a.x
+    df_sub_scaled(R.rh, R.rl, -cih, -cil, a.y);   // + ci a.y
+    df_sub_scaled(R.ih, R.il, crh, crl, a.y);     // - cr a.y
+    df_sub_scaled(R.ih, R.il, cih, cil, a.x);     // - ci a.x
+  } else if constexpr (std::is_same<V, double>::value) {
+    R.t -= cs[k] * a;
+  } else {
+    const double cr = cs[2 * k], ci = cs[2 * k + 1];
+    R.r -= cr * a.x - ci * a.y;
+    R.i -= cr * a.y + ci * a.x;
+  }
+}
+
+// w[i] (and wlo[i]) from R, rounded once; ||w||^2 accumulated
+template <typename V>
+__device__ __forceinline__ void row_store(const Row<V> &R, V *w, V *wlo, int64_t i, float &nh,
+                                          float &nl, double &nrm) {
+  if constexpr (std::is_same<V, float>::value) {
+    float o, r;
+    df_store(R.h, R.l, o, r);
+    w[i] = o;
+    if (wlo) wlo[i] = r; else r = 0.f;
+    df_add_sq(nh, nl, o, r);
+  } else if constexpr (std::is_same<V, float2>::value) {
+    V o, r;
+    df_store(R.rh, R.rl, o.x, r.x);
+    df_store(R.ih, R.il, o.y, r.y);
+    w[i] = o;
+    if (wlo) wlo[i] = r; else { r.x = 0.f; r.y = 0.f; }
+    df_add_sq(nh, nl, o.x, r.x);
+    df_add_sq(nh, nl, o.y, r.y);
+  } else if constexpr (std::is_same<V, double>::value) {
+    w[i] = R.t;
+    nrm += R.t * R.t;
+  } else {
+    V o;
+    o.x = R.r;
+    o.y = R.i;
+    w[i] = o;
+    nrm += R.r * R.r + R.i * R.i;
+  }
+}
+
+// w <- w - sum_k c_k u_k, rounded once; partial[blk] = the block's ||w||^2.  fp32 vectors:
+// every coefficient split into two fp32 words and the sum carried in double-float; fp64
+// vectors: fp64.  Every row subtracts c_0 u_0, c_1 u_1, ... in that order; the loads of
+// kK vectors for U rows are issued before the arithmetic that uses them.
+template <typename V>
+__global__ void __launch_bounds__(kThreads, 4) update_kernel(VecSet S, const double *c, V *w,
                                                           V *wlo, int64_t n, double *partial) {
   using A = typename Rv<V>::A;
   constexpr bool kC = Rv<V>::cplx;
   constexpr bool kF = std::is_same<A, float>::value;
   constexpr int P = kC ? 2 : 1;
+  constexpr int U = RowsPer<V>::U;
+  constexpr int kK = 8;
   extern __shared__ double cs[];   // [m][P] fp64, then (fp32 vectors) [m][P][2] words
   float *cf = reinterpret_cast<float *>(cs + S.m * P);
   for (int t = threadIdx.x; t < S.m * P; t += kThreads) {
@@ -174,58 +294,35 @@ __global__ void __launch_bounds__(kThreads) update_kernel(VecSet S, const double
   __syncthreads();
   float nh = 0.f, nl = 0.f;
   double nrm = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kThreads) {
-    if constexpr (kF && kC) {
-      const V w0 = w[i];
-      float rh = w0.x, rl = 0.f, ih = w0.y, il = 0.f;
-      if (wlo) { const V l0 = wlo[i]; rl = l0.x; il = l0.y; }
-#pragma unroll 4
-      for (int k = 0; k < S.m; k++) {
-        const V a = vec<V>(S, k)[i];
-        const float crh = cf[4 * k], crl = cf[4 * k + 1], cih = cf[4 * k + 2], cil = cf[4 * k + 3];
-        df_sub_scaled(rh, rl, crh, crl, a.x);     // - cr a.x
-        df_sub_scaled(rh, rl, -cih, -cil, a.y);   // + ci a.y
-        df_sub_scaled(ih, il, crh, crl, a.y);     // - cr a.y
-        df_sub_scaled(ih, il, cih, cil, a.x);     // - ci a.x
-      }
-      V o, r;
-      df_store(rh, rl, o.x, r.x);
-      df_store(ih, il, o.y, r.y);
-      w[i] = o;
-      if (wlo) wlo[i] = r; else { r.x = 0.f; r.y = 0.f; }
-      df_add_sq(nh, nl, o.x, r.x);
-      df_add_sq(nh, nl, o.y, r.y);
-    } else if constexpr (kF) {
-      float hi = w[i], lo = wlo ? wlo[i] : 0.f;
-#pragma unroll 4
-      for (int k = 0; k < S.m; k++) df_sub_scaled(hi, lo, cf[2 * k], cf[2 * k + 1], vec<V>(S, k)[i]);
-      float o, r;
-      df_store(hi, lo, o, r);
-      w[i] = o;
-      if (wlo) wlo[i] = r; else r = 0.f;
-      df_add_sq(nh, nl, o, r);
-    } else if constexpr (kC) {
-      double wr = w[i].x, wi = w[i].y;
-#pragma unroll 4
-      for (int k = 0; k < S.m; k++) {
-        const V a = vec<V>(S, k)[i];
-        const double cr = cs[2 * k], ci = cs[2 * k + 1];
-        wr -= cr * a.x - ci * a.y;
-        wi -= cr * a.y + ci * a.x;
-      }
-      V o;
-      o.x = wr;
-      o.y = wi;
-      w[i] = o;
-      nrm += wr * wr + wi * wi;
-    } else {
-      double t = w[i];
-#pragma unroll 8
-      for (int k = 0; k < S.m; k++) t -= cs[k] * vec<V>(S, k)[i];
-      w[i] = t;
-      nrm += t * t;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  for (; i + (U - 1) * stride < n; i += U * stride) {
+    Row<V> R[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) R[u] = row_load<V>(w, wlo, i + u * stride);
+    for (int k = 0; k < S.m; k += kK) {
+      V a[kK][U];
+#pragma unroll
+      for (int kk = 0; kk < kK; kk++)
+        if (k + kk < S.m) {
+          const V *uk = vec<V>(S, k + kk);
+#pragma unroll
+          for (int u = 0; u < U; u++) a[kk][u] = uk[i + u * stride];
+        }
+#pragma unroll
+      for (int kk = 0; kk < kK; kk++)
+        if (k + kk < S.m) {
+#pragma unroll
+          for (int u = 0; u < U; u++) row_sub<V>(R[u], cs, cf, k + kk, a[kk][u]);
+        }
     }
+#pragma unroll
+    for (int u = 0; u < U; u++) row_store<V>(R[u], w, wlo, i + u * stride, nh, nl, nrm);
+  }
+  for (; i < n; i += stride) {
+    Row<V> R = row_load<V>(w, wlo, i);
+    for (int k = 0; k < S.m; k++) row_sub<V>(R, cs, cf, k, vec<V>(S, k)[i]);
+    row_store<V>(R, w, wlo, i, nh, nl, nrm);
   }
   if constexpr (kF) nrm = df_value(nh, nl);
   block_sum_store(nrm, partial, blockIdx.x);
