@@ -573,16 +573,21 @@ __device__ __forceinline__ bool find_rep_simple(const Sm2 &S, const TwoParams &P
 // A term's value goes back to its row by a segmented inclusive scan over the 32 lanes
 // (rows are non-decreasing along a list, so equal neighbouring rows form one segment);
 // the lane holding a segment's last term adds the sum to the row's shared accumulator.
-// Every step has a fixed order, so the product is deterministic; no atomics.
+// A round holds terms of one chunk only, so a row has at most kTileChunk terms in it and
+// log2(kTileChunk) scan steps cover every segment.  Every step has a fixed order, so the
+// product is deterministic; no atomics.  The accumulators of fp32 rows are double-float
+// pairs: this GPU's fp64 pipe is slow enough that one fp64 update per segment of every
+// round kept it 30% busy.
 // ---------------------------------------------------------------------------------------
-// weights of the term-parallel kernel (shared memory): fp32 vectors use, per coupling
-// class c and stabiliser order t, J_c / 2 sqrt(t) split into two fp32 words, and for
-// complex sectors (cos, remainder, sin, remainder) per character; fp64 vectors use the
-// fp64 tables
+// weights of the term-parallel kernel (shared memory): per coupling class c and
+// stabiliser order t, J_c / 2 sqrt(t), split into two fp32 words for fp32 vectors and as
+// one fp64 word for fp64 vectors (in the same 8-byte slots); complex fp32 sectors add
+// (cos, remainder, sin, remainder) per character, complex fp64 sectors use the fp64
+// character table
 struct TileW {
   const float2 *wf;
   const float4 *csf4;
-  const double *sqd, *csd;
+  const double *csd;
   int n_sq;
 };
 
@@ -646,7 +651,7 @@ __device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, con
             v_im = fmaf(crh, xj.y, fmaf(crl, xj.y, fmaf(cih, xj.x, cil * xj.x)));
           }
         } else {
-          const double wgt = P.jh[c] * W.sqd[R.t];   // J_c / 2 sqrt(|Stab_j|)
+          const double wgt = reinterpret_cast<const double *>(W.wf)[c * W.n_sq + R.t];   // J_c / 2 sqrt(|Stab_j|)
           if constexpr (!kC) {
             const double pv = wgt * xj;
             v_re = R.ph == 0 ? pv : -pv;
@@ -666,10 +671,11 @@ __device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, con
     if (defer) list[*n_def + __popc(dm & ((1u << lane) - 1u))] = (uint16_t)e;
     *n_def += __popc(dm);
   }
-  // segmented inclusive scan: lanes with the same row form one segment (fp32 values are
-  // summed in double-float, so the sum of a segment carries no fp32 rounding)
+  // segmented inclusive scan: lanes with the same row form one segment, at most kTileChunk
+  // lanes long (fp32 values are summed in double-float, so the sum of a segment carries
+  // no fp32 rounding)
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
+  for (int d = 1; d < kTileChunk; d <<= 1) {
     const int ru = __shfl_up_sync(FULL, r, d);
     const A a = __shfl_up_sync(FULL, v_re, d);
     A b = 0;
@@ -696,8 +702,23 @@ __device__ __forceinline__ void tile_round(const Sm2 &S, const TwoParams &P, con
   const int rn = __shfl_down_sync(FULL, r, 1);
   __syncwarp();   // the previous round's accumulator updates are visible
   if (r < 32 && (lane == 31 || rn != r)) {   // last lane of its segment
-    racc[r] += (double)v_re + (double)l_re;
-    if constexpr (kC) racc[32 + r] += (double)v_im + (double)l_im;
+    if constexpr (kF) {
+      float *rf = reinterpret_cast<float *>(racc);
+      float h = rf[r], l = rf[32 + r];
+      df_add(h, l, v_re);
+      rf[r] = h;
+      rf[32 + r] = __fadd_rn(l, l_re);
+      if constexpr (kC) {
+        h = rf[64 + r];
+        l = rf[96 + r];
+        df_add(h, l, v_im);
+        rf[64 + r] = h;
+        rf[96 + r] = __fadd_rn(l, l_im);
+      }
+    } else {
+      racc[r] += (double)v_re + (double)l_re;
+      if constexpr (kC) racc[32 + r] += (double)v_im + (double)l_im;
+    }
   }
 }
 
@@ -715,7 +736,8 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
     for (uint32_t k = threadIdx.x; k < (uint32_t)P.n_classes * P.n_sq; k += blockDim.x) {
       const double wv = P.jh[k / P.n_sq] * sqd[k % P.n_sq];
       const float hi = (float)wv;
-      wf[k] = make_float2(hi, (float)(wv - (double)hi));
+      if (sizeof(typename Vf<V>::A) == 4) wf[k] = make_float2(hi, (float)(wv - (double)hi));
+      else reinterpret_cast<double *>(wf)[k] = wv;
     }
     if (kC)
       for (uint32_t k = threadIdx.x; k < P.n_cs / 2; k += blockDim.x) {
@@ -732,7 +754,6 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
   TileW W;
   W.wf = reinterpret_cast<const float2 *>(sm + P.off_sqf);
   W.csf4 = reinterpret_cast<const float4 *>(sm + P.off_csf);
-  W.sqd = reinterpret_cast<const double *>(sm + P.off_sq);
   W.csd = reinterpret_cast<const double *>(sm + P.off_cs);
   W.n_sq = (int)P.n_sq;
   using A = typename Vf<V>::A;
@@ -741,7 +762,9 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned char *tw = sm + P.off_tile + (size_t)wid * kTileWarpBytes;
   uint64_t *rowst = reinterpret_cast<uint64_t *>(tw);
-  double *racc = reinterpret_cast<double *>(tw + 32 * 8);          // [2][32] re, im
+  // row accumulators: fp64 [re 32][im 32], or for fp32 rows double-float words as floats
+  // [re hi 32][re lo 32][im hi 32][im lo 32]
+  double *racc = reinterpret_cast<double *>(tw + 32 * 8);
   uint16_t *list = reinterpret_cast<uint16_t *>(tw + 32 * 8 + 32 * 16);
   const V *x = reinterpret_cast<const V *>(P.x);
   V *y = reinterpret_cast<V *>(P.y);
@@ -807,7 +830,8 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
     if (valid) {
       const int64_t i = P.r0 + (tile << 5) + lane;
       const double rs = rsd[__ldcs(P.stab + i)];
-      const double row_re = (double)racc[lane];
+      const float *rf = reinterpret_cast<const float *>(racc);
+      const double row_re = kF ? (double)rf[lane] + (double)rf[32 + lane] : (double)racc[lane];
       // y_i in fp64, rounded once to the vector type; for fp32 vectors the rounding's
       // remainder goes to ylo when asked (the mixed Lanczos keeps y as a double-float
       // pair for its update), and <x, y> uses the unrounded value
@@ -819,7 +843,7 @@ __global__ void __launch_bounds__(kE2 ? kTileThreadsE2 : kTileThreads, kE2 ? 1 :
         if (kF && P.ylo) reinterpret_cast<float *>(P.ylo)[i - P.r0] = (float)(yd - (double)yi);
         if (P.partial) dot_re += xi * (kF && P.ylo ? yd : (double)yi);
       } else {
-        const double row_im = (double)racc[32 + lane];
+        const double row_im = kF ? (double)rf[64 + lane] + (double)rf[96 + lane] : (double)racc[32 + lane];
         const V xv = x[i];
         const double yr = diag * (double)xv.x + row_re * rs;
         const double yim = diag * (double)xv.y + row_im * rs;
