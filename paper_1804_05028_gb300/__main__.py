@@ -3,7 +3,10 @@
     python -m paper_1804_05028_gb300 describe NAME [--n-up K] [-o FILE]
         write the descriptor of a built-in sector (chain16, square36, tilted40) as JSON
     python -m paper_1804_05028_gb300 run FILE [--dtype f64|f32] [--max-steps M] [--tol T]
+                                         [--fixed-steps K] [--reorth local|none|full]
         build the sector's basis on the current GPU, run Lanczos, print one JSON line
+        (--fixed-steps runs exactly K steps; --reorth full keeps the whole Krylov basis
+        on the device and sweeps against it)
 
 A descriptor holds the fields of a sector: sites, sublattice count, bonds and their
 coupling classes, the group as site permutations (and optional spin-flip bits), the
@@ -63,9 +66,11 @@ def _run(args) -> int:
         real = B.is_real
         dt = {"f64": torch.float64 if real else torch.complex128,
               "f32": torch.float32 if real else torch.complex64}[args.dtype]
-        r = B.lanczos(dtype=dt, max_steps=args.max_steps, tol=args.tol)
+        r = B.lanczos(dtype=dt, max_steps=args.max_steps, tol=args.tol,
+                      fixed_steps=args.fixed_steps, reorth=args.reorth)
         out.update({"E0": r["E0"], "steps": r["steps"], "converged": r["converged"],
-                    "dtype": args.dtype, "ms_total": r["ms_total"], "ms_apply": r["ms_apply"]})
+                    "dtype": args.dtype, "reorth": args.reorth, "ms_total": r["ms_total"],
+                    "ms_apply": r["ms_apply"], "ms_reorth": r["ms_reorth"]})
     print(json.dumps(out))
     B.close()
     return 0
@@ -83,6 +88,8 @@ def main(argv=None) -> int:
     a.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     a.add_argument("--max-steps", type=int, default=400)
     a.add_argument("--tol", type=float, default=1e-13)
+    a.add_argument("--fixed-steps", type=int, default=0)
+    a.add_argument("--reorth", choices=["local", "none", "full"], default="local")
     args = ap.parse_args(argv)
     try:
         return _describe(args) if args.cmd == "describe" else _run(args)

@@ -73,3 +73,9 @@ def test_run_chain16_ground_state(tmp_path):
         d = json.loads(r.stdout.strip().splitlines()[-1])
         assert d["dim"] == bs.size and d["converged"]
         assert abs(d["E0"] - e_ref) <= tol * abs(e_ref)
+    # full reorthogonalisation and a fixed step count
+    r = _cli("run", str(f), "--dtype", "f32", "--reorth", "full", "--fixed-steps", "40")
+    assert r.returncode == 0, r.stderr
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["steps"] == 40 and d["reorth"] == "full" and d["ms_reorth"] > 0
+    assert abs(d["E0"] - e_ref) <= 1e-6 * abs(e_ref)
