@@ -44,6 +44,9 @@ struct ed_batch {
   bool all_full = false;     // every sector has a one-sublattice (whole) table
   int cls_off[ED_MAXCLS + 1];
   double jh[ED_MAXCLS], jzq[ED_MAXCLS];
+  const uint32_t *nib = nullptr;   // the first basis's nibble tables (shared lattice)
+  int n_nib = 0;
+  int cls_word[ED_MAXCLS + 1];
   int rows_per_item = 0;   // chosen tile
   int64_t n_items = 0;
   int sm_count = 0;
@@ -66,6 +69,9 @@ struct BatchParams {
   int n_classes;
   int cls_off[ED_MAXCLS + 1];
   float jh[ED_MAXCLS], jzq[ED_MAXCLS];
+  const uint32_t *nib;             // antiparallel masks by nibbles, [word][n_nib][16]
+  int n_nib;
+  int cls_word[ED_MAXCLS + 1];     // words of class c: [cls_word[c], cls_word[c + 1])
 };
 
 __device__ __forceinline__ int sector_of(const BatchParams &P, int64_t item) {
@@ -135,7 +141,7 @@ static_assert(sizeof(BatchSector) % 4 == 0, "sector descriptors are copied as 32
 
 // kFull: every sector looks its representatives up in a whole table (one sublattice), so
 // the block-wise search is not compiled in and the kernel needs far fewer registers.
-// Resident blocks per SM: 6 up to k = 4; 5 for k = 8 (51 registers, a 16-byte spill),
+// Resident blocks per SM: 6 up to k = 4; 5 for k = 8 (48 registers and a small spill),
 // which beat 4 (63 registers) by 5% and 6 (42 registers) by 3%.
 template <int K, bool kFull>
 __global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 5) : 1)
@@ -175,72 +181,83 @@ __global__ void __launch_bounds__(kBatchThreads, kFull ? (K <= 4 ? 6 : 5) : 1)
       for (int c = 0; c < P.n_classes; c++) {
         const float jh = P.jh[c];   // the class's J/2 goes into every term's weight
         int nanti = 0;
-        for (int b = P.cls_off[c]; b < P.cls_off[c + 1]; b++) {
-          const int pa = bond_s[2 * b], pb = bond_s[2 * b + 1];
-          if ((((s >> pa) ^ (s >> pb)) & 1ULL) == 0) continue;
-          nanti++;
-          const uint64_t s2 = s ^ ((1ULL << pa) | (1ULL << pb));
-          RepOut R;
-          if constexpr (kFull) {
-            const uint64_t e = __ldg(S.T.full + s2);
-            R.rep = e & 0xFFFFFFFFull;
-            R.g = (int)((e >> 32) & 0xFFFF);
-            R.t = (int)(e >> 48);
-          } else {
-            R = find_rep(S.T, S.T.rep, S.T.sym_off, S.T.sym_list, S.T.dest, S.T.phase, s2);
-            if (R.mixed) continue;
-          }
-          const int64_t j = kFull ? lookup_index32(S.I, (uint32_t)R.rep) : lookup_index(S.I, R.rep);
-          if (j < 0) continue;
-          float w = jh;
-          if (R.t != 1) w *= __ldg(S.sqrt_f + R.t);   // t = |Stab| of the target, mostly 1
-          const int ph = __ldg(S.T.phase + R.g);
-          if (!S.cplx) {
-            const float sg = ph == 0 ? w : -w;
-            const float *xr = reinterpret_cast<const float *>(S.x) + j * K;
-            if constexpr (K % 8 == 0) {
-#pragma unroll
-              for (int v = 0; v < K; v += 8) {
-                const F8 q = ld8(xr + v);
-#pragma unroll
-                for (int u = 0; u < 8; u++) yr[v + u] += sg * q.v[u];
-              }
-            } else if constexpr (K % 4 == 0) {
-#pragma unroll
-              for (int v = 0; v < K; v += 4) {
-                const float4 q = *reinterpret_cast<const float4 *>(xr + v);
-                yr[v] += sg * q.x; yr[v + 1] += sg * q.y; yr[v + 2] += sg * q.z; yr[v + 3] += sg * q.w;
-              }
+        for (int wd = P.cls_word[c]; wd < P.cls_word[c + 1]; wd++) {
+          const int b0 = P.cls_off[c] + (wd - P.cls_word[c]) * 32;
+          // the row's antiparallel bonds among b0 .. b0 + 31 as a mask (XOR of the state's
+          // nibbles' table entries), then one pass per set bit: lanes run the term body
+          // together instead of one bond test at a time (with a branch per bond, about
+          // half the lanes of every term body were idle)
+          uint32_t am = 0;
+          const uint32_t *nw = P.nib + (uint32_t)wd * P.n_nib * 16;
+          for (int q = 0; q < P.n_nib; q++) am ^= __ldg(nw + q * 16 + (uint32_t)((s >> (4 * q)) & 15u));
+          nanti += __popc(am);
+          while (am) {
+            const int b = b0 + __ffs(am) - 1;
+            am &= am - 1;
+            const int pa = bond_s[2 * b], pb = bond_s[2 * b + 1];
+            const uint64_t s2 = s ^ ((1ULL << pa) | (1ULL << pb));
+            RepOut R;
+            if constexpr (kFull) {
+              const uint64_t e = __ldg(S.T.full + s2);
+              R.rep = e & 0xFFFFFFFFull;
+              R.g = (int)((e >> 32) & 0xFFFF);
+              R.t = (int)(e >> 48);
             } else {
-#pragma unroll
-              for (int v = 0; v < K; v++) yr[v] += sg * xr[v];
+              R = find_rep(S.T, S.T.rep, S.T.sym_off, S.T.sym_list, S.T.dest, S.T.phase, s2);
+              if (R.mixed) continue;
             }
-          } else {
-            const float cr = __ldg(S.cs_f + 2 * ph) * w, ci = __ldg(S.cs_f + 2 * ph + 1) * w;
-            const float2 *xc = reinterpret_cast<const float2 *>(S.x) + j * K;
-            if constexpr (K % 4 == 0) {   // four complex entries per 32-byte load
-#pragma unroll
-              for (int v = 0; v < K; v += 4) {
-                const F8 q = ld8(reinterpret_cast<const float *>(xc + v));
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                  yr[v + u] += cr * q.v[2 * u] - ci * q.v[2 * u + 1];
-                  yi[v + u] += cr * q.v[2 * u + 1] + ci * q.v[2 * u];
+            const int64_t j = kFull ? lookup_index32(S.I, (uint32_t)R.rep) : lookup_index(S.I, R.rep);
+            if (j < 0) continue;
+            float w = jh;
+            if (R.t != 1) w *= __ldg(S.sqrt_f + R.t);   // t = |Stab| of the target, mostly 1
+            const int ph = __ldg(S.T.phase + R.g);
+            if (!S.cplx) {
+              const float sg = ph == 0 ? w : -w;
+              const float *xr = reinterpret_cast<const float *>(S.x) + j * K;
+              if constexpr (K % 8 == 0) {
+  #pragma unroll
+                for (int v = 0; v < K; v += 8) {
+                  const F8 q = ld8(xr + v);
+  #pragma unroll
+                  for (int u = 0; u < 8; u++) yr[v + u] += sg * q.v[u];
                 }
-              }
-            } else if constexpr (K % 2 == 0) {   // two complex entries per 16-byte load
-#pragma unroll
-              for (int v = 0; v < K; v += 2) {
-                const float4 q = *reinterpret_cast<const float4 *>(xc + v);
-                yr[v] += cr * q.x - ci * q.y;
-                yi[v] += cr * q.y + ci * q.x;
-                yr[v + 1] += cr * q.z - ci * q.w;
-                yi[v + 1] += cr * q.w + ci * q.z;
+              } else if constexpr (K % 4 == 0) {
+  #pragma unroll
+                for (int v = 0; v < K; v += 4) {
+                  const float4 q = *reinterpret_cast<const float4 *>(xr + v);
+                  yr[v] += sg * q.x; yr[v + 1] += sg * q.y; yr[v + 2] += sg * q.z; yr[v + 3] += sg * q.w;
+                }
+              } else {
+  #pragma unroll
+                for (int v = 0; v < K; v++) yr[v] += sg * xr[v];
               }
             } else {
-              const float2 q = xc[0];
-              yr[0] += cr * q.x - ci * q.y;
-              yi[0] += cr * q.y + ci * q.x;
+              const float cr = __ldg(S.cs_f + 2 * ph) * w, ci = __ldg(S.cs_f + 2 * ph + 1) * w;
+              const float2 *xc = reinterpret_cast<const float2 *>(S.x) + j * K;
+              if constexpr (K % 4 == 0) {   // four complex entries per 32-byte load
+  #pragma unroll
+                for (int v = 0; v < K; v += 4) {
+                  const F8 q = ld8(reinterpret_cast<const float *>(xc + v));
+  #pragma unroll
+                  for (int u = 0; u < 4; u++) {
+                    yr[v + u] += cr * q.v[2 * u] - ci * q.v[2 * u + 1];
+                    yi[v + u] += cr * q.v[2 * u + 1] + ci * q.v[2 * u];
+                  }
+                }
+              } else if constexpr (K % 2 == 0) {   // two complex entries per 16-byte load
+  #pragma unroll
+                for (int v = 0; v < K; v += 2) {
+                  const float4 q = *reinterpret_cast<const float4 *>(xc + v);
+                  yr[v] += cr * q.x - ci * q.y;
+                  yi[v] += cr * q.y + ci * q.x;
+                  yr[v + 1] += cr * q.z - ci * q.w;
+                  yi[v + 1] += cr * q.w + ci * q.z;
+                }
+              } else {
+                const float2 q = xc[0];
+                yr[0] += cr * q.x - ci * q.y;
+                yi[0] += cr * q.y + ci * q.x;
+              }
             }
           }
         }
@@ -309,6 +326,9 @@ int launch(ed_batch *Bt, int rows_per_item, cudaStream_t st) {
   P.bond = Bt->d_bond;
   P.n_classes = Bt->n_classes;
   for (int c = 0; c <= Bt->n_classes; c++) P.cls_off[c] = Bt->cls_off[c];
+  for (int c = 0; c <= Bt->n_classes; c++) P.cls_word[c] = Bt->cls_word[c];
+  P.nib = Bt->nib;
+  P.n_nib = Bt->n_nib;
   for (int c = 0; c < Bt->n_classes; c++) { P.jh[c] = (float)Bt->jh[c]; P.jzq[c] = (float)Bt->jzq[c]; }
   ED_CK(cudaMemsetAsync(Bt->d_counter, 0, 8, st));
   const int grid = Bt->sm_count * 8;
@@ -351,6 +371,9 @@ extern "C" int ed_batch_create(ed_basis *const *bases, int32_t n, const double *
   Bt->sm_count = b0->sm_count;
   Bt->bases.assign(bases, bases + n);
   for (int c = 0; c <= b0->n_classes; c++) Bt->cls_off[c] = b0->cls_off[c];
+  for (int c = 0; c <= b0->n_classes; c++) Bt->cls_word[c] = b0->cls_word[c];
+  Bt->nib = b0->d_nib;
+  Bt->n_nib = b0->n_nib;
   for (int c = 0; c < b0->n_classes; c++) { Bt->jh[c] = 0.5 * J[c]; Bt->jzq[c] = 0.25 * J[c] * Jz[c]; }
   Bt->host.resize(n);
   std::vector<float> ftab;
