@@ -53,10 +53,18 @@ KERNEL_SOURCES = ["paper_1804_05028_gb300/csrc/apply.cu",
                   "paper_1804_05028_gb300/csrc/capi.cu"]
 
 
+def _code_only(src: str) -> str:
+    """The source without comments and with whitespace collapsed, so that a comment edit
+    does not detach the committed counters from the code they were taken on."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return " ".join(src.split())
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,5 +1,4 @@
-// apply_fast.cu -- the row-pull product y = H x with a two-level representative search,
-// one thread per row and one exchange term at a time.
+// apply_fast.cu -- the row-pull product y = H x with a two-level representative search.
 //
 // Two-level search.  In Alg. 2 of arXiv:1804.05028 the candidates of a minimal block Y
 // are Sym_Y(s_Y) = K_R h: the coset of the stabiliser K_R = {k in G_0 : k R = R} of
@@ -8,18 +7,22 @@
 // problem (Eqs. 8-10) for the group K_R acting on blocks 1.., with block 1 in the role
 // of block 0.  Level 1 looks up (Rep_X, h) per block, applies h once; level 2 looks up
 // (Rep^R_X, Sym^R_X) of the images and scans only those candidates.  The candidate
-// scans that dominate a warp's time (the longest Sym list among 32 lanes) shrink from
-// ~20 to ~3 entries on the 6x6 C4v sector.  Every minimiser of the orbit is still
-// visited (all of them lie in the scanned sets), so |Stab| and the character check are
-// exact, as in the single-level search.
+// scans shrink from ~20 to ~3 entries on the 6x6 C4v sector.  Every minimiser of the
+// orbit is still visited (all of them lie in the scanned sets), so |Stab| and the
+// character check are exact, as in the single-level search.
 //
-// Per row (one thread): the row's blocks are extracted once; antiparallel bonds come as
-// 32-bit masks (one coupling class per word); each exchange flips one bit in the block of
-// each end.  Tables: Rep_X / first of Sym_X, stabiliser ids, the level-2 tables (when
-// they fit), prefix ranks, bonds and norms in shared memory; SymmetryAction_X in global
-// memory (L1/L2), and the level-2 tables there too when they do not fit.  The index of
-// the representative: prefix rank, Limits bucket, binary search of the narrow postfixes.  fp32 vectors are summed per row with a compensated
-// (two-float) accumulator, fp64 in fp64.  Each y_i written once; no atomics.
+// Two kernels share the search:
+//   apply_tile_kernel  the product: a warp owns 32 consecutive rows and resolves their
+//                      exchange terms 32 at a time from term lists in shared memory (see
+//                      the comment above tile_round); the index of a representative is
+//                      one ranked Limits record (first index + popcount of a bitmap).
+//   apply_two_kernel   one thread per row, one term at a time; it serves the
+//                      class-resolved expectations <x|H_c|x> (the adjoint).
+// Antiparallel bonds come as 32-bit masks (one coupling class per word), from per-nibble
+// XOR tables; each exchange flips one bit in the block of each end.  Tables: Rep_X /
+// first of Sym_X, stabiliser ids, the level-2 tables (when they fit), prefix ranks,
+// bonds and weights in shared memory; SymmetryAction_X in global memory (L1/L2), and the
+// level-2 tables there too when they do not fit.  Each y_i is written once; no atomics.
 #include "sced_internal.cuh"
 #include "dfloat.cuh"
 #include <algorithm>
