@@ -15,7 +15,11 @@
 // Index.  top_rank compresses the occupied values of the top r bits to a dense rank;
 // key = rank << q | next q bits; limits[key] = first position whose key is >= key
 // (lower bound in the sorted basis); the remaining low bits go to a narrow postfix
-// array searched inside the bucket.
+// array searched inside the bucket.  Where they fit (4x the basis's bytes, or 64 MB),
+// ranked records replace the search: one record per prefix rank and value of every bit
+// but the low 6, holding the first basis position and a 64-bit bitmap of the low-6-bit
+// values present, so that the index is first + popcount(bitmap below the value) -- one
+// 16-byte load.
 #include "sced_internal.cuh"
 #include <algorithm>
 #include <chrono>
