@@ -241,6 +241,7 @@ void or_rows_slots(const or_problem *P, const uint64_t *basis, const int32_t *st
       const int cls = P->bond_class[b];
       if (spin(s_i, P->N, a) == spin(s_i, P->N, c)) { d += 0.25 * P->J[cls] * P->Jz[cls]; continue; }
       d -= 0.25 * P->J[cls] * P->Jz[cls];
+      if (P->J[cls] == 0.0) continue;   /* no exchange in this class: no off-diagonal entry */
       const uint64_t sp = s_i ^ (1ULL << (P->N - 1 - a)) ^ (1ULL << (P->N - 1 - c));
       uint64_t rep;
       int32_t h, nm;

@@ -309,3 +309,24 @@ def test_stored_matrix_ground_state_and_term_count():
     e_full = spla.eigsh(Hf, k=1, which="SA")[0][0]
     e, _, _, _ = oracle.lanczos(S.matvec, w.state_uniform(bs, 1805))
     assert abs(e - e_full) < 1e-10
+
+
+@pytest.mark.parametrize("p", [
+    w.square_torus(4, momentum=(0, 0), point_irrep=0, J2=0.5, n_sublat=4, n_up=8),
+    w.square_torus(4, momentum=(1, 0), point_irrep=1, J2=0.5, n_sublat=2, n_up=8),
+], ids=lambda p: p.name)
+def test_stored_matrix_by_coupling_class(p):
+    """H is linear in the exchange of each class (Eq. 21): the stored matrices built with
+    one class's exchange alone (the other set to zero, which stores no entry for its
+    bonds) add up, weighted by J_c, to the literal Eq. 2 projection of the whole H.  Their
+    entry counts add up to the whole matrix's."""
+    Hp, bs, _ = oracle.projected_hamiltonian(p)
+    parts = []
+    for c in range(p.n_classes):
+        J = [0.0] * p.n_classes
+        J[c] = 1.0
+        S = oracle.stored_matrix(p.with_couplings(J, p.Jz))
+        parts.append((S, _dense_from_matvec(S, bs.size, not p.is_real())))
+    M = sum(p.J[c] * parts[c][1] for c in range(p.n_classes))
+    assert np.abs(M - Hp).max() < 1e-12
+    assert sum(S.nnz for S, _ in parts) == oracle.stored_matrix(p).nnz
