@@ -977,15 +977,17 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
     if (L.own_ylo) cudaFree(L.ylo);
     return ed_fail(ED_ERR_OOM, "cannot allocate the reorthogonalisation scratch");
   }
-  ED_CK(cudaEventCreate(&L.e0));
-  ED_CK(cudaEventCreate(&L.e1));
-  ED_CK(cudaEventCreate(&L.r0));
-  ED_CK(cudaEventCreate(&L.r1));
+  if (cudaEventCreate(&L.e0) != cudaSuccess || cudaEventCreate(&L.e1) != cudaSuccess ||
+      cudaEventCreate(&L.r0) != cudaSuccess || cudaEventCreate(&L.r1) != cudaSuccess) {
+    cudaGetLastError();
+    rc = ed_fail(ED_ERR_CUDA, "cannot create the timing events");
+  }
   std::vector<double> alpha, alpha_rec, beta;
   double E0 = 0;
   int steps = 0, conv = 0;
-  rc = lanczos_pass(L, &o, max_steps, o.fixed_steps > 0, tol, alpha, alpha_rec, beta, &E0, &steps,
-                    &conv, nullptr, nullptr);
+  if (!rc)
+    rc = lanczos_pass(L, &o, max_steps, o.fixed_steps > 0, tol, alpha, alpha_rec, beta, &E0,
+                      &steps, &conv, nullptr, nullptr);
   if (!rc && o.psi) {
     const int m = (int)alpha.size();
     std::vector<double> bt(beta.begin(), beta.begin() + std::max(0, m - 1));
@@ -1030,10 +1032,8 @@ extern "C" int ed_lanczos(ed_basis *B, const double *J, const double *Jz,
   if (own) for (int k = 0; k < 3; k++) cudaFree(L.v[k]);
   if (L.own_ylo) cudaFree(L.ylo);
   if (L.d_ro) cudaFree(L.d_ro);
-  cudaEventDestroy(L.e0);
-  cudaEventDestroy(L.e1);
-  cudaEventDestroy(L.r0);
-  cudaEventDestroy(L.r1);
+  for (cudaEvent_t e : {L.e0, L.e1, L.r0, L.r1})
+    if (e) cudaEventDestroy(e);
   res->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return rc;
 }
