@@ -202,6 +202,24 @@ def cpu_baseline(p, seconds: float, seed: int = 7):
                       f"(matrix-free brute-force rows, fp64), {nnz} nonzeros in {dt:.1f}s"}
 
 
+def stored_matrix_record(workload: str):
+    """The oracle's stored-matrix product (the alternative of Sec. IV) as timed when the
+    committed oracle E0 of this workload was written (tests/golden), for context: the
+    28 GB matrix takes over an hour to build, so it is not rebuilt here."""
+    path = os.path.join(ROOT, "tests", "golden", f"{workload}_e0.json")
+    if not os.path.exists(path):
+        return None
+    g = json.load(open(path))
+    m = g.get("stored_matrix_product")
+    if not m:
+        return None
+    return {"value": m["nonzeros_per_s"], "unit": UNIT, "cores": m["cores"],
+            "seconds_per_product": m["seconds"], "build_seconds": g.get("build_seconds"),
+            "host": m.get("host"), "kind": "oracle stored matrix (CSR), fp64",
+            "note": "timed on the host that wrote " + os.path.relpath(path, ROOT) +
+                    ", not in this run"}
+
+
 def bench_batch(ed, torch, steps: int):
     """All 572 sectors of the 5x5 J1-J2 torus (S^z = 1/2 .. 25/2, every momentum and
     little-group 1-D irrep) in one persistent, graph-replayed launch with block vectors
@@ -525,6 +543,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p, args.cpu_seconds)
+        sm = stored_matrix_record(args.workload)
+        if sm:
+            cpu["stored_matrix"] = sm
 
     if rank == 0:
         r = main_res
