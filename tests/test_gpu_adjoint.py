@@ -1,6 +1,9 @@
 """dE0/dJ through the adjoint product: class-resolved expectations against the oracle,
 torch.autograd against central finite differences (h = 1e-4, fp64) and against the
 Hellmann-Feynman value from the oracle's dense ground state."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -122,6 +125,21 @@ def test_dE0_dJ_mixed_against_oracle():
     assert abs(1.0 * g[0] + 0.5 * g[1] - ev[0]) <= 2e-5, (g, ev[0])
 
 
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _oracle_e0_square36(J2):
+    """The oracle's ground-state energy of the 6x6 sector at J2 (J1 = 1), from the
+    committed golden files written by tests/golden/make_square36_e0.py (J2 = 0.5) and
+    make_square36_scan.py (0.40, 0.45, 0.55, 0.60)."""
+    if abs(J2 - 0.5) < 1e-12:
+        return json.load(open(os.path.join(GOLDEN, "square36_e0.json")))["E0"]
+    for e in json.load(open(os.path.join(GOLDEN, "square36_scan_e0.json")))["scan"]:
+        if abs(e["J2"] - J2) < 1e-12:
+            return e["E0"]
+    raise KeyError(J2)
+
+
 @pytest.fixture(scope="module")
 def square36():
     B = _ed().build_basis_from(w.config_square36(0.5))
@@ -140,11 +158,14 @@ def test_dE0_dJ_square36_scan(square36, J2):
     measured, not assumed: with steps h = 1e-4 and 2h, fd(2h) - fd(h) is three times the
     error of fd(h) to leading order, and the Richardson combination (4 fd(h) - fd(2h)) / 3
     removes it.  The autograd value must agree with the Richardson value to 2e-7 and with
-    fd(h) within fd(h)'s own measured truncation error (plus 2e-7)."""
+    fd(h) within fd(h)'s own measured truncation error (plus 2e-7).  The forward E0 is
+    the oracle's (stored matrix, fp64 Lanczos) within 1e-10."""
     from paper_1804_05028_gb300.autograd import ground_state_energy
     B = square36
     J = torch.tensor([1.0, J2], dtype=torch.float64, requires_grad=True)
     E = ground_state_energy(B, J)
+    e_or = _oracle_e0_square36(J2)
+    assert abs(E.item() - e_or) <= 1e-10 * abs(e_or), (J2, E.item(), e_or)
     E.backward()
     g = J.grad.numpy()
     h = 1e-4

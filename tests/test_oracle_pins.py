@@ -330,3 +330,22 @@ def test_stored_matrix_by_coupling_class(p):
     M = sum(p.J[c] * parts[c][1] for c in range(p.n_classes))
     assert np.abs(M - Hp).max() < 1e-12
     assert sum(S.nnz for S, _ in parts) == oracle.stored_matrix(p).nnz
+
+
+def test_square36_golden_energies_concave_in_J2():
+    """The committed oracle energies of the 6x6 sector (tests/golden): E0(J2) is the
+    minimum over states of <psi|H_1 + J2 H_2|psi>, a minimum of affine functions of J2,
+    so it is concave: every second difference over the scan J2 = 0.40 .. 0.60 is <= 0
+    (up to the energies' 1e-13 convergence).  The class-split matrices hold together
+    exactly the entries of the whole matrix at J2 = 0.5."""
+    import json
+    import os
+    gdir = os.path.join(os.path.dirname(__file__), "golden")
+    g5 = json.load(open(os.path.join(gdir, "square36_e0.json")))
+    gs = json.load(open(os.path.join(gdir, "square36_scan_e0.json")))
+    assert gs["dim"] == g5["dim"] == 31566122
+    assert sum(gs["offdiag_terms_per_class"]) == g5["offdiag_terms"]
+    pts = sorted([(e["J2"], e["E0"]) for e in gs["scan"]] + [(0.5, g5["E0"])])
+    assert [round(j, 2) for j, _ in pts] == [0.40, 0.45, 0.50, 0.55, 0.60]
+    e = np.array([v for _, v in pts])
+    assert np.all(e[:-2] - 2 * e[1:-1] + e[2:] <= 1e-12 * np.abs(e[1:-1]))
