@@ -337,11 +337,18 @@ def run_reference(args):
         _, nt, _, _ = oracle.columns(p, step_rows[k])
         nnz += int(nt.sum()) + step_rows[k].size
     value = nnz / dt
+    cfg = {"workload": args.workload, "description": desc, "dim": oracle.dimension_formula(p),
+           "n_sublat": p.n_sublat, "n_sym": p.n_sym, "rows_per_step": n_rows}
+    gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}_e0.json")
+    if os.path.exists(gpath):   # the oracle's own term count of the whole sector
+        g = json.load(open(gpath))
+        cfg["offdiag_terms_per_product"] = g["offdiag_terms"]
+        cfg["nonzeros_per_product"] = g["dim"] + g["offdiag_terms"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (state-keyed uniform[-1,1) vectors, seed 1804)",
-            "config": {"workload": args.workload, "description": desc, "rows_per_step": n_rows},
+            "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": f"{n_rows} sampled representative rows per step, matrix-free brute force"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
