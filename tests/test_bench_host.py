@@ -61,3 +61,33 @@ def test_profiled_counters_follow_the_source_hash(tmp_path, monkeypatch):
     assert bench.profiled("demo", "warp_instructions_per_launch", "mixed") is None
     assert bench.profiled("demo", "traffic_bytes_per_launch", "f64") is None
     assert bench.profiled("absent", "traffic_bytes_per_launch", "mixed") is None
+
+
+def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
+    """The counters' key follows the code, not its comments or layout."""
+    src = tmp_path / "k.cu"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", ["k.cu"])
+    src.write_text("int f(int a) { return a + 1; }  // one\n")
+    h0 = bench.kernel_hash()
+    src.write_text("/* header */\nint f(int a) {\n  return a + 1;   // two\n}\n")
+    assert bench.kernel_hash() == h0
+    src.write_text("int f(int a) { return a + 2; }\n")
+    assert bench.kernel_hash() != h0
+
+
+def test_reference_config_names_the_sector():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0", "--workload", "chain16"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    cfg = json.loads(out.stdout.strip().splitlines()[-1])["config"]
+    assert cfg["workload"] == "chain16" and cfg["dim"] == 810
+    assert cfg["n_sublat"] >= 1 and cfg["n_sym"] == 16
+
+
+def test_stored_matrix_record_from_golden():
+    rec = bench.stored_matrix_record("square36")
+    assert rec is not None and rec["value"] > 0 and rec["cores"] >= 1
+    assert "not in this run" in rec["note"]
+    assert bench.stored_matrix_record("chain16") is None
