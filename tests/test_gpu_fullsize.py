@@ -181,3 +181,30 @@ def test_square36_e0_against_oracle():
     r32 = B.lanczos(dtype=torch.float32, seed=1805)
     assert abs(r32["E0"] - g["E0"]) <= 1e-9 * abs(g["E0"]), (r32["E0"], g["E0"])
     B.close()
+
+
+def test_square36_product_against_oracle_stored_matrix():
+    """H x on the whole 6x6 J1-J2 sector against the oracle's stored-matrix product
+    (tests/golden/square36_hv.json, written by tests/golden/make_square36_hv.py from
+    oracle/ alone), x the state-keyed vector with seed 1804, fp64: <x, y>, ||y||^2 and the
+    sums of y over 256 row blocks (every row, in aggregate) within 1e-12 of the scale of
+    the quantity (the sum of |y| over the block), and y at 1024 sampled rows within
+    1e-12 max|y|."""
+    import paper_1804_05028_gb300 as ed
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "square36_hv.json")))
+    B = ed.build_basis_from(w.config_square36(0.5))
+    assert B.dim == g["dim"] and B.count_terms()[1] == g["offdiag_terms"]
+    s, _ = B.export()
+    x = w.state_uniform(s, 1804)
+    y = B.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
+    B.close()
+    ymax = np.abs(y).max()
+    scale_dot = float(np.abs(x) @ np.abs(y))
+    assert abs(float(x @ y) - g["x_dot_y"]) <= 1e-12 * scale_dot
+    assert abs(float(y @ y) - g["y_norm2"]) <= 1e-12 * float(y @ y)
+    blk = g["block_rows"]
+    for k, a in enumerate(range(0, g["dim"], blk)):
+        seg = y[a:a + blk]
+        assert abs(float(seg.sum()) - g["block_sums"][k]) <= 1e-12 * g["abs_block_sums"][k], k
+    rows = np.array(g["sample_rows"])
+    assert np.abs(y[rows] - np.array(g["sample_y"])).max() <= 1e-12 * ymax
