@@ -208,3 +208,24 @@ def test_square36_product_against_oracle_stored_matrix():
         assert abs(float(seg.sum()) - g["block_sums"][k]) <= 1e-12 * g["abs_block_sums"][k], k
     rows = np.array(g["sample_rows"])
     assert np.abs(y[rows] - np.array(g["sample_y"])).max() <= 1e-12 * ymax
+
+
+def test_square36_fp32_product_against_oracle_stored_matrix():
+    """The fp32 product (the mixed form's) on the same vector, rounded to fp32 first,
+    against the oracle's fp64 stored-matrix product.  Rounding x to fp32 moves each entry
+    by at most u |x_j| (u = 2^-24) and the product rounds y_i once, so every row is within
+    2u sum_j |H_ij| |x_j| + u |y_i| <= 1e-6 max|y| here, and every block sum within 1e-6
+    of the block's sum of |y|."""
+    import paper_1804_05028_gb300 as ed
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "square36_hv.json")))
+    B = ed.build_basis_from(w.config_square36(0.5))
+    s, _ = B.export()
+    x = w.state_uniform(s, 1804)
+    y = B.apply_H(torch.from_numpy(x).float().cuda()).cpu().numpy().astype(np.float64)
+    B.close()
+    ymax = np.abs(y).max()
+    blk = g["block_rows"]
+    for k, a in enumerate(range(0, g["dim"], blk)):
+        assert abs(float(y[a:a + blk].sum()) - g["block_sums"][k]) <= 1e-6 * g["abs_block_sums"][k], k
+    rows = np.array(g["sample_rows"])
+    assert np.abs(y[rows] - np.array(g["sample_y"])).max() <= 1e-6 * ymax
