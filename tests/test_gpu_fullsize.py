@@ -94,11 +94,13 @@ def _check_sector(p, n_basis_samples, n_config_samples, n_rows):
 
 
 def test_square36_j1j2_gamma_a1():
-    _check_sector(w.config_square36(), 3000, 20000, 400)
+    _check_sector(w.config_square36(), 3000, 20000, 20000)
 
 
 def test_tilted40_gamma_a():
-    _check_sector(w.config_tilted40(), 2000, 10000, 200)
+    """The 40-site sector's product on 1e5 seeded rows (its stored matrix would not fit
+    in host memory)."""
+    _check_sector(w.config_tilted40(), 2000, 10000, 100000)
 
 
 def test_square36_spin_flip_even_odd():
