@@ -11,13 +11,16 @@ row in aggregate and some rows one by one:
 
 * <x, y>, ||y||^2 and sum(y);
 * the sums of y over 256 consecutive row blocks of equal length (the last shorter);
-* y at 1024 rows drawn with numpy's default_rng(1806).
+* y at 1024 rows drawn with numpy's default_rng(1806), and the basis states of those
+  rows.
 
 It takes about 80 minutes on 8 host cores.  Run from the repository root:
 
-    python tests/golden/make_square36_hv.py [--cache DIR]
+    python tests/golden/make_square36_hv.py [--cache DIR] [--states-only]
 
 ``--cache DIR`` reads or keeps the oracle basis there (basis.npy, stab.npy).
+``--states-only`` adds the sampled rows' basis states to an existing file without
+rebuilding the matrix.
 """
 from __future__ import annotations
 
@@ -48,6 +51,7 @@ def log(msg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--cache", default=None)
+    ap.add_argument("--states-only", action="store_true")
     args = ap.parse_args()
     p = workloads.config_square36(0.5)
     t_all = time.time()
@@ -65,6 +69,14 @@ def main():
             np.save(os.path.join(args.cache, "stab.npy"), stab)
     assert bs.size == oracle.dimension_formula(p)
     D = bs.size
+    if args.states_only:
+        out = json.load(open(OUT))
+        out["sample_states"] = [int(v) for v in bs[np.array(out["sample_rows"])]]
+        with open(OUT, "w") as f:
+            json.dump(out, f)
+            f.write("\n")
+        log(f"added the sampled rows' states to {OUT}")
+        return
     S = oracle.stored_matrix(p, (bs, stab), chunk_rows=1 << 20,
                              progress=lambda r, n: log(f"  rows {r}/{n}")
                              if r % (1 << 24) < (1 << 20) or r == n else None)
@@ -84,6 +96,7 @@ def main():
            "abs_block_sums": [float(np.abs(y[a:a + blk]).sum()) for a in range(0, D, blk)],
            "sample_seed": 1806, "sample_rows": [int(r) for r in rows],
            "sample_y": [float(v) for v in y[rows]],
+           "sample_states": [int(v) for v in bs[rows]],
            "host": f"{platform.machine()} {oracle.max_threads()} threads",
            "total_seconds": time.time() - t_all}
     with open(OUT, "w") as f:

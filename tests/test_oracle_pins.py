@@ -349,3 +349,26 @@ def test_square36_golden_energies_concave_in_J2():
     assert [round(j, 2) for j, _ in pts] == [0.40, 0.45, 0.50, 0.55, 0.60]
     e = np.array([v for _, v in pts])
     assert np.all(e[:-2] - 2 * e[1:-1] + e[2:] <= 1e-12 * np.abs(e[1:-1]))
+
+
+def test_square36_stored_matrix_product_against_matrix_free_rows():
+    """The committed oracle product on the 6x6 sector (tests/golden/square36_hv.json, from
+    the stored matrix, CSR rows built with targets found by binary search in the basis)
+    against the oracle's other path, matrix-free rows with the representative and the
+    index of every term found anew (Eqs. 3-5), on the file's 1024 sampled rows: the same
+    values to 1e-12 of max|y|.  The sampled states are representatives of the sector, the
+    file's block sums add up to its total, and |<x, y>| <= ||x|| ||y|| with
+    ||x||^2 <= D / 3 (a plausibility bound: x is uniform on [-1, 1))."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "square36_hv.json")))
+    p = w.config_square36(0.5)
+    states = np.array(g["sample_states"], dtype=np.uint64)
+    rep, _, _, kept = oracle.representatives(p, states)
+    assert np.array_equal(rep, states) and np.all(kept)
+    assert np.all(np.diff(states.astype(np.float64)) > 0)   # sorted rows, sorted basis
+    y = oracle.rows(p, states, lambda q: w.state_uniform(q, 1804))
+    ref = np.array(g["sample_y"])
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert abs(sum(g["block_sums"]) - g["y_sum"]) <= 1e-9 * sum(g["abs_block_sums"])
+    assert abs(g["x_dot_y"]) <= np.sqrt(g["dim"] / 3 * 1.01 * g["y_norm2"])
